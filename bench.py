@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the long-range two-electron-integral (LR-TEI) tensorized approximation on GB300.
+
+One step = one full assembly of the N_b^2 x N_b^2 long-range tensor B of the 180-function
+s/p/d workload (12 atoms in a 12 bohr cube, 3s+2p+1d contracted shells of 3 primitives,
+omega = 0.4, n = 24 Chebyshev nodes per dimension, P = 32 Gauss-Legendre nodes): the plan's
+factors (nodes, Chebyshev coefficients, pair table, moments) are resident in HBM; the step
+runs the contraction and writes all 32400^2 FP64 entries.  A J-build rate on 32 densities of
+the same molecule is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision P]
+
+Under torchrun (N > 1) each rank assembles its own copy (independent problems, weak scaling,
+no data-path collective); value = entries of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LR-TEI entries/s & J-builds/s at ≤1e-7 rel err, mixed vs FP64 same GPU"
+UNIT = "entries/s"
+WORKLOAD = ("nb180_spd: 12 atoms in a 12 bohr cube, 3s+2p+1d Cartesian shells x 3 primitives (N_b=180), "
+            "exponents log-uniform [0.05, 2e3], omega=0.4, n=24, P=32; full 32400x32400 FP64 B per step")
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured figure in MEASURED_PEAKS.json)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp64", "fp32", "bf16"])
+    ap.add_argument("--form", default="factored", choices=["auto", "hadamard", "factored"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-jbuild", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, enabled: bool = True):
+        self.dev = device_index
+        self.enabled = enabled
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        if not self.enabled:
+            return
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_source_hash(rel):
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel: str, workload: str, src_rel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the kernel (profiles/dram_traffic.md rows: | kernel | workload | bytes | hash |)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash(src_rel)
+    for ln in open(p):
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload and cells[3] == cur:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+# ------------------------------------------------------------------ the oracle on host cores
+
+def cpu_oracle_rate(mol, budget_s: float, seed: int = 99):
+    """Entries/s of the FP64 oracle (Algorithm 1 per entry, moments of the pairs involved
+    included) on a bounded random sample of entries of the workload, all host cores."""
+    import numpy as np
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    nbf = mol.nbf
+    count = 64
+    total_entries, total_t = 0, 0.0
+    while True:
+        o = oracle.Oracle.from_molecule(mol)
+        idx = rng.integers(0, nbf, size=(count, 4)).astype(np.int32)
+        t0 = time.perf_counter()
+        o.entries(idx, threads=threads)
+        dt = time.perf_counter() - t0
+        total_entries += count
+        total_t += dt
+        del o
+        if total_t >= budget_s * 0.5 or count >= 1 << 22:
+            break
+        remaining = budget_s - total_t
+        rate = count / max(dt, 1e-6)
+        count = int(min(max(count * 2, rate * remaining * 0.9), 1 << 22))
+        if remaining <= 0.5:
+            break
+    return total_entries / total_t, threads, f"{total_entries} random entries (mu,nu,ka,la) of B, Algorithm 1 per entry incl. their pair moments, {total_t:.1f} s"
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2210_13069_gb300 import build_lib, lrtei, synth
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    if rank == 0 or not os.path.exists(lrtei.library_path()):
+        build_lib.build()
+    barrier(world)
+    mol = synth.workload_spd(natoms=args.natoms)
+    nbf = mol.nbf
+    nb2 = nbf * nbf
+    entries_per_step = float(nb2) * nb2
+    npair = nbf * (nbf + 1) // 2
+    n3 = mol.n ** 3
+    stream = torch.cuda.current_stream()
+
+    plan = lrtei.Plan(mol, args.precision)
+    B = torch.empty((nb2, nb2), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        plan.assemble_B(args.form, out=B)
+    torch.cuda.synchronize()
+    plan.status()
+
+    lrtei.lrtei_profile_reset()
+    lrtei.lrtei_profile_enable(True)
+    sampler = ClockSampler(local, enabled=not args.no_clocks)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.assemble_B(args.form, out=B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    launches = lrtei.lrtei_profile_get("*")[1]
+    prof = {}
+    for name in ("tc_gemm", "gemm_fp64", "gemm_fp32", "hadamard", "kron", "expand_B", "split"):
+        prof[name] = lrtei.lrtei_profile_get(name)
+    lrtei.lrtei_profile_enable(False)
+    lrtei.lrtei_profile_reset()
+    plan.status()
+    ms = max_over_ranks(ms_local, world, device="cuda")
+    value = world * entries_per_step / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    form_used = plan.info and lrtei.lrtei_plan_info_get(plan.plan)["last_form"]
+    if args.precision in ("split_bf16", "bf16"):
+        kname, src = "tc_gemm", "paper_2210_13069_gb300/csrc/k_tcgen05.cu"
+        k_slices = 6 if args.precision == "split_bf16" else 1
+        tot_ms, cnt = prof["tc_gemm"]
+        # algorithmic flops per step of the tensor-core GEMMs: G = F K (npair x n3 x n3) and the
+        # upper-triangular tiles of B_u = G F^T (npair^2 n3), one product each
+        flops_step = 2.0 * npair * n3 * n3 + 1.0 * npair * npair * n3
+        peak = peaks["bf16_tflops_sustained"]
+        unit, bound = "TFLOP/s", "tensor"
+    elif args.precision == "fp32":
+        kname, src = "gemm_fp32", "paper_2210_13069_gb300/csrc/k_gemm.cu"
+        tot_ms, cnt = prof["gemm_fp32"]
+        flops_step = 2.0 * npair * npair * n3
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        unit, bound, k_slices = "TFLOP/s", "alu", 1
+    elif form_used == 1:
+        kname, src = "hadamard", "paper_2210_13069_gb300/csrc/k_hadamard.cu"
+        tot_ms, cnt = prof["hadamard"]
+        Ibar2 = (lrtei.lrtei_plan_info_get(plan.plan)["nrows"] / npair) ** 2
+        flops_step = npair * npair * mol.P * Ibar2 * (6 * mol.n + 3)
+        peak, unit, bound, k_slices = FP64_PEAK_TFLOPS, "TFLOP/s", "alu", 1
+    else:
+        kname, src = "gemm_fp64", "paper_2210_13069_gb300/csrc/k_gemm.cu"
+        tot_ms, cnt = prof["gemm_fp64"]
+        flops_step = 2.0 * npair * npair * n3
+        peak, unit, bound, k_slices = FP64_PEAK_TFLOPS, "TFLOP/s", "alu", 1
+    roofline = None
+    if cnt > 0 and tot_ms > 0:
+        per_launch_flops = flops_step * args.steps / cnt
+        avg_ms = tot_ms / cnt
+        achieved = per_launch_flops / (avg_ms / 1e3) / 1e12
+        traffic = profiled_traffic(kname, "nb180_spd", src)
+        roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind if bound == "tensor" else
+                    "nominal FP64/FP32 rate (not in MEASURED_PEAKS.json)", "launches_per_step": cnt / args.steps,
+                    "avg_launch_ms": avg_ms, "share_of_step": tot_ms / (ms_local * args.steps),
+                    "split_products": k_slices,
+                    "issued_frac": achieved * k_slices / peak}
+
+    # ---- J-builds/s (32 densities), same plan
+    jb = None
+    if not args.no_jbuild:
+        R = 32
+        D = torch.as_tensor(synth.random_densities(4242, nbf, R), device="cuda")
+        J = torch.empty_like(D)
+        for _ in range(2):
+            plan.jbuild(D, out=J)
+        torch.cuda.synchronize()
+        j0 = torch.cuda.Event(enable_timing=True)
+        j1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        j0.record(stream)
+        for _ in range(reps):
+            plan.jbuild(D, out=J)
+        j1.record(stream)
+        torch.cuda.synchronize()
+        jms = j0.elapsed_time(j1) / reps
+        jb = {"value": world * R / (max_over_ranks(jms, world, device="cuda") / 1e3), "unit": "J-builds/s",
+              "densities": R, "ms_per_batch": jms}
+        del D, J
+
+    # ---- end to end through the public API: host basis in, host B out (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hostB = torch.empty((nb2, nb2), dtype=torch.float64, pin_memory=True)
+        centers, ls, nprim, exps, coefs = mol.packed()
+        h2d = centers.nbytes + ls.nbytes + nprim.nbytes + exps.nbytes + coefs.nbytes
+        times = []
+        for it in range(2):
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = lrtei.Plan(mol, args.precision)
+            p2.assemble_B(args.form, out=B)
+            hostB.copy_(B, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            p2.close()
+            if it > 0:
+                times.append(dt)
+        dt = max_over_ranks(min(times), world, device="cuda")
+        e2e = {"value": world * entries_per_step / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(nb2 * nb2 * 8), "s_per_step": dt}
+        del hostB
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(mol, budget_s=15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        dtype = {"split_bf16": "bf16x3 (8-bit slices, fp32 acc)", "bf16": "bf16", "fp64": "f64", "fp32": "f32"}[
+            args.precision]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded molecule, no dataset)",
+            "config": {"workload": WORKLOAD if args.natoms == 12 else f"nb{15 * args.natoms}_spd (scaled)",
+                       "precision": args.precision, "form": args.form,
+                       "form_used": {1: "hadamard", 2: "factored"}.get(form_used, str(form_used)),
+                       "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
+                       "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
+                       "parallelism": f"replicas x{world} (independent problems)"},
+            "jbuilds": jb, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+
+def run_reference(args, world, rank, local):
+    if rank != 0:
+        return
+    from paper_2210_13069_gb300 import synth
+    import oracle
+    oracle.build()
+    mol = synth.workload_spd(natoms=args.natoms)
+    budget = 8.0
+    rates = []
+    cores = os.cpu_count() or 1
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        rate, cores, sample = cpu_oracle_rate(mol, budget_s=budget, seed=1000 + i)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = statistics.median(rates)
+    nb2 = mol.nbf ** 2
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": nb2 * nb2 / value * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded molecule, no dataset)",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)", "form": "hadamard (Algorithm 1)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores, "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/* lrtei.h -- C ABI of the GB300 (sm_103a) library for the tensorized approximation (TA) of the
+ * long-range two-electron integrals tensor B^lr (Badreddine, Chollet, Grigori, arXiv 2210.13069).
+ *
+ * What the library computes (paper references are to that article):
+ *   B^lr(mu,nu,ka,la) = int int g_mu(x) g_nu(x) erf(w|x-y|)/|x-y| g_ka(y) g_la(y) dx dy over a box
+ *   (Section 1, eq. "long-range" and eq. "compact"), approximated by
+ *     K(x,y) ~ (w/sqrt(pi)) sum_p w_p prod_d sum_{a,b} A_d^(p)(a,b) T_a(u_d) T_b(v_d)
+ *   (Section 3.1, eq. TEI2, eq. chebcheb, eq. Approx_kernel), which gives Theorem 1:
+ *     B(mu nu, ka la) = (w/sqrt(pi)) sum_p w_p sum_{j,j'} c_j c_j' prod_d (S_d A_d^(p) S_d^T)(j, j')
+ *   with S_d the 1D moment matrices of eq. defV, and its Khatri-Rao factored form (eq. tensors)
+ *     B = (w/sqrt(pi)) sum_p w_p M (A_x^(p) (x) A_y^(p) (x) A_z^(p)) M^T,
+ *   which applies B to densities (J-builds, Section 5, eq. coulapprox) without forming it.
+ *
+ * Conventions shared by every call:
+ *   - Basis: contracted Cartesian Gaussians (eq. "basis", "primi").  A shell of angular momentum
+ *     l expands into its (l+1)(l+2)/2 components in the order lx = l..0, ly = l-lx..0,
+ *     lz = l-lx-ly.  Each component is normalised on R^3; each contraction to unit norm.
+ *   - Box: per dimension [lo_d, hi_d]; NULL selects the default cube centred on the atoms'
+ *     extent with half-width (half extent + sqrt(ln(1e16) / (2 alpha_min))).
+ *   - Chebyshev nodes of the first kind, n per dimension, degrees 0..n-1 (Definition 1).
+ *   - Gauss-Legendre nodes z_p, weights w_p on [-1,1]; s_p = w (1 + z_p)/2 (eq. TEI2).
+ *   - B is the mode-(1,2) unfolding: row mu*N_b + nu, column ka*N_b + la, row-major, 0-based.
+ *   - Every compute call is asynchronous on the CUDA stream it is given (NULL = legacy default
+ *     stream).  Device pointers (d_*) are owned by the caller; the library owns plans and their
+ *     workspaces.  Inputs are validated on the host before anything is launched; a failed
+ *     call returns a status and leaves a message for lrtei_last_error().  Device-side failures
+ *     (a bounded wait that gave up, a non-finite value) are latched in the plan and reported by
+ *     lrtei_plan_status(), which synchronises the plan's stream.
+ *   - No call falls back to the CPU: without a usable CUDA device every call that computes
+ *     returns LRTEI_ERR_CUDA.
+ */
+#ifndef LRTEI_H
+#define LRTEI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRTEI_OK = 0,
+  LRTEI_ERR_ARG = 1,         /* invalid argument (checked on the host before any launch) */
+  LRTEI_ERR_ALLOC = 2,       /* device or host allocation failed */
+  LRTEI_ERR_CUDA = 3,        /* a CUDA runtime call failed (no device, launch failure ...) */
+  LRTEI_ERR_TIMEOUT = 4,     /* a device-side bounded wait gave up */
+  LRTEI_ERR_NUMERIC = 5,     /* a non-finite value was detected on the device */
+  LRTEI_ERR_UNSUPPORTED = 6  /* valid but not supported by this build (e.g. size limits) */
+} lrtei_status;
+
+/* Arithmetic of the contractions (moments, nodes, Chebyshev coefficients and the node sum
+ * are FP64 in every mode). */
+typedef enum {
+  LRTEI_FP64 = 0,        /* FP64 CUDA-core contractions */
+  LRTEI_FP32 = 1,        /* FP32 CUDA-core contractions */
+  LRTEI_SPLIT_BF16 = 2,  /* tcgen05 tensor cores, operands split into three 8-bit BF16 slices
+                            with per-row power-of-two scales, FP32 accumulation that is exact
+                            within each 256-deep K chunk, integer/FP32 accumulation across chunks */
+  LRTEI_BF16 = 3         /* tcgen05 tensor cores, one BF16 slice per operand (about 1e-3) */
+} lrtei_precision;
+
+/* Which of the two equivalent forms of Theorem 1 assembles B. */
+typedef enum {
+  LRTEI_FORM_AUTO = 0,      /* cost model: Hadamard when 3 P Ibar^2 <= n^2, else factored */
+  LRTEI_FORM_HADAMARD = 1,  /* entry-wise Hadamard form (Theorem 1 / Algorithm 1) */
+  LRTEI_FORM_FACTORED = 2   /* Khatri-Rao factored form (eq. tensors) */
+} lrtei_form;
+
+typedef struct lrtei_basis lrtei_basis;
+typedef struct lrtei_plan lrtei_plan;
+
+typedef struct {
+  int nbf;          /* N_b */
+  int64_t npair;    /* unique basis pairs mu <= nu: N_b (N_b + 1) / 2 */
+  int64_t nrows;    /* primitive-pair rows over unique pairs: sum_{mu<=nu} I_mu I_nu */
+  int n, P;
+  double omega;
+  double box_lo[3], box_hi[3];
+  int precision;    /* lrtei_precision */
+  int last_form;    /* lrtei_form used by the last lrtei_assemble_B call */
+  size_t workspace_bytes; /* device bytes the plan currently holds */
+} lrtei_plan_info;
+
+/* ---- basis (Section 1, eq. "basis"/"primi") ------------------------------------------
+ * Host arrays, copied: centers[3*nshells] (bohr), l[nshells] in 0..4, nprim[nshells] in 1..16,
+ * exps/coefs concatenated in shell order (sum(nprim) each, exps > 0).  Returns LRTEI_ERR_ARG
+ * on invalid input. */
+lrtei_status lrtei_basis_create(int nshells, const double* centers, const int* l, const int* nprim,
+                                const double* exps, const double* coefs, lrtei_basis** out);
+void lrtei_basis_destroy(lrtei_basis* basis);
+int lrtei_basis_nbf(const lrtei_basis* basis);
+
+/* ---- plan (Section 3.1: w, box, n = N^(1/3), P = N_q1) --------------------------------
+ * Uploads the basis and computes, on the device and on `stream`: Gauss-Legendre nodes and
+ * weights (eq. TEI2), the Chebyshev coefficient matrices A_d^(p) (Definition 1, eq. chebcheb),
+ * the primitive-pair table (Proposition 1) and the moment matrices S_d (eq. defV).
+ * omega > 0; 1 <= n <= 64; 1 <= P <= 128; box_lo/box_hi: 3 doubles each or both NULL. */
+lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
+                               const double* box_hi, lrtei_precision precision, void* stream, lrtei_plan** out);
+void lrtei_plan_destroy(lrtei_plan* plan);
+lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info);
+/* Synchronises the plan's stream and returns the latched device-side status (then clears it). */
+lrtei_status lrtei_plan_status(lrtei_plan* plan);
+
+/* ---- full tensor (Theorem 1; eq. tensors) ----------------------------------------------
+ * Writes all N_b^2 x N_b^2 entries of B, FP64, row-major with leading dimension ld >= N_b^2,
+ * into the caller's device buffer d_B.  `form` selects the Hadamard or the factored form. */
+lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, int64_t ld, void* stream);
+
+/* Rows [row_begin, row_end) of the unique-pair matrix B_u (rows and columns are unique pairs
+ * mu <= nu in the order (0,0),(0,1)..(0,N_b-1),(1,1)..), FP64, leading dimension ld >= npair.
+ * B(mu nu, ka la) = B_u(pair(min,max), pair(min,max)). */
+lrtei_status lrtei_assemble_Bu_rows(lrtei_plan* plan, lrtei_form form, int64_t row_begin, int64_t row_end,
+                                    double* d_Bu, int64_t ld, void* stream);
+
+/* ---- entries (Algorithm 1) ---------------------------------------------------------------
+ * d_idx4: device int32[4*count] of (mu, nu, ka, la); d_out: device double[count]. */
+lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out, void* stream);
+
+/* ---- factors (Theorem 1: w_p, s_p, A^(p), W~ = S_d) ---------------------------------------
+ * Any pointer may be NULL.  d_s, d_w: P doubles; d_C: 3*P*n*n (d, p, a, b); d_S: 3*nrows*n
+ * (d, row, m), rows ordered by unique pair then j = j1*I_nu + j2; d_c: nrows coefficients c_j. */
+lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d_s, double* d_w, double* d_c,
+                           void* stream);
+
+/* ---- J-build (Section 5, eq. coulapprox in the density form J = mat(B vec(D))) ----------
+ * d_D: R symmetric N_b x N_b densities (FP64, row-major, consecutive); d_J: same shape.
+ * J_r(mu, nu) = sum_{ka, la} B(mu nu, ka la) D_r(ka, la), through the factored form, never
+ * forming B.  Uses the plan's precision for the two M-contractions. */
+lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream);
+
+/* ---- batched J-builds (many molecules of uneven size in one graph-captured launch) -------
+ * plans[nmol]: plans (each with its own omega, n, P); d_D[m], d_J[m], R[m]: per-molecule
+ * densities and outputs.  All plans must share the precision.  On the first call for a set of
+ * plans the library captures the whole batch into one CUDA graph; later calls with the same
+ * plans and pointers replay it. */
+lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,
+                                  double* const* d_J, void* stream);
+
+/* ---- the (n, P) selector (a 3-layer MLP, FP32, trained on the GPU) ----------------------
+ * Features (6): omega, box half-width, log10 alpha_min, log10 alpha_max, max l, log10 target.
+ * Outputs (2): n, P (rounded, clamped to [8, 64] x [8, 96]).  Training data are error sweeps
+ * of the plain method (see the Python layer).  Weights live on the device. */
+typedef struct lrtei_selector lrtei_selector;
+lrtei_status lrtei_selector_create(int hidden, uint64_t seed, lrtei_selector** out);
+void lrtei_selector_destroy(lrtei_selector* sel);
+/* One epoch of mini-batch Adam on (d_X[N*6], d_Y[N*2]) (device, FP32, normalised targets).
+ * Returns the mean loss of the epoch in *loss (synchronises). */
+lrtei_status lrtei_selector_train_epoch(lrtei_selector* sel, const float* d_X, const float* d_Y, int N, int batch,
+                                        float lr, float* loss, void* stream);
+/* Forward pass for N rows: d_X[N*6] -> d_Yhat[N*2] (device). */
+lrtei_status lrtei_selector_forward(lrtei_selector* sel, const float* d_X, float* d_Yhat, int N, void* stream);
+/* Forward + backward of the mean squared error for N rows; gradients to d_grad (device,
+ * lrtei_selector_nparams floats, packed W1,b1,W2,b2,W3,b3). */
+lrtei_status lrtei_selector_grad(lrtei_selector* sel, const float* d_X, const float* d_Y, int N, float* d_grad,
+                                 float* loss, void* stream);
+int64_t lrtei_selector_nparams(const lrtei_selector* sel);
+/* Parameters to / from host memory (packed as above), for checkpointing. */
+lrtei_status lrtei_selector_get_params(const lrtei_selector* sel, float* h_params);
+lrtei_status lrtei_selector_set_params(lrtei_selector* sel, const float* h_params);
+
+/* ---- kernel timing (tracing) ----------------------------------------------------------
+ * When enabled, the library records a pair of CUDA events on the launching stream around each
+ * launch of its main kernels ("tc_gemm", "gemm_fp64", "gemm_fp32", "hadamard", "kron",
+ * "expand_B", "moments", "build_F", "split", "jbuild").  lrtei_profile_get synchronises those
+ * events and returns the summed device time and the launch count of one kernel name.
+ * Off by default; process-wide; not thread-safe against concurrent enable/reset. */
+lrtei_status lrtei_profile_enable(int on);
+lrtei_status lrtei_profile_get(const char* kernel, double* total_ms, int64_t* launches);
+void lrtei_profile_reset(void);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* lrtei_last_error(void);
+/* Library version string. */
+const char* lrtei_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRTEI_H */

@@ -1,0 +1,208 @@
+// k_factored.cu -- kernels of the Khatri-Rao factored form (eq. tensors) and its application:
+//   M(mu nu, (m1 n + m2) n + m3) = sum_{j in mu nu} c_j S_x(j, m1) S_y(j, m2) S_z(j, m3)
+//   B = (w/sqrt(pi)) M K M^T,  K = sum_p w_p A_x^(p) (x) A_y^(p) (x) A_z^(p)
+// K is applied either densely (tensor-core path) or by three mode products per node (eq. ig1).
+// Also the symmetric expansion of the unique-pair matrix B_u into the full N_b^2 x N_b^2 B and
+// the density packing of the J-build (Section 5).
+#include "lrtei_internal.h"
+
+namespace lrtei {
+
+__device__ __forceinline__ int64_t pair_idx(int nbf, int a, int b) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return (int64_t)lo * nbf - (int64_t)lo * (lo - 1) / 2 + (hi - lo);
+}
+
+// One block (x) per pair r in [r0, r1); threads over the n^3 columns.
+template <typename T>
+__global__ void k_build_F(int n, int64_t nrows, const int64_t* __restrict__ pair_row, const double* __restrict__ row_c,
+                          const double* __restrict__ S, int64_t r0, T* __restrict__ F, int64_t ldF) {
+  const int64_t r = r0 + blockIdx.x;
+  const int64_t j0 = pair_row[r], j1 = pair_row[r + 1];
+  const int n3 = n * n * n;
+  const double* Sx = S;
+  const double* Sy = S + (size_t)nrows * n;
+  const double* Sz = S + 2 * (size_t)nrows * n;
+  T* out = F + (size_t)blockIdx.x * ldF;
+  for (int m = threadIdx.x; m < n3; m += blockDim.x) {
+    const int m1 = m / (n * n), m2 = (m / n) % n, m3 = m % n;
+    double acc = 0.0;
+    for (int64_t j = j0; j < j1; ++j)
+      acc += row_c[j] * Sx[(size_t)j * n + m1] * Sy[(size_t)j * n + m2] * Sz[(size_t)j * n + m3];
+    out[m] = (T)acc;
+  }
+}
+
+template <typename T>
+void launch_build_F(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, T* d_F, int64_t ldF,
+                    cudaStream_t st) {
+  int64_t nr = r1 - r0;
+  while (nr > 0) {
+    int64_t chunk = nr > (1LL << 30) ? (1LL << 30) : nr;
+    count_launch();
+    k_build_F<T><<<(unsigned)chunk, 256, 0, st>>>(n, t.nrows, t.pair_row, t.row_c, d_S, r0, d_F, ldF);
+    r0 += chunk;
+    d_F += chunk * ldF;
+    nr -= chunk;
+  }
+}
+template void launch_build_F<double>(const PairTable&, int, const double*, int64_t, int64_t, double*, int64_t,
+                                     cudaStream_t);
+template void launch_build_F<float>(const PairTable&, int, const double*, int64_t, int64_t, float*, int64_t,
+                                    cudaStream_t);
+
+// K(a, b) with a = (a1 n + a2) n + a3, b likewise; one thread per entry.
+__global__ void k_build_K(int n, int P, const double* __restrict__ C, const double* __restrict__ w,
+                          double* __restrict__ K) {
+  const int n3 = n * n * n;
+  const int64_t total = (int64_t)n3 * n3;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / n3), b = (int)(t % n3);
+    const int a1 = a / (n * n), a2 = (a / n) % n, a3 = a % n;
+    const int b1 = b / (n * n), b2 = (b / n) % n, b3 = b % n;
+    const size_t nn = (size_t)n * n;
+    double acc = 0.0;
+    for (int p = 0; p < P; ++p) {
+      const double* cx = C + ((size_t)0 * P + p) * nn;
+      const double* cy = C + ((size_t)1 * P + p) * nn;
+      const double* cz = C + ((size_t)2 * P + p) * nn;
+      acc += w[p] * cx[a1 * n + b1] * cy[a2 * n + b2] * cz[a3 * n + b3];
+    }
+    K[t] = acc;
+  }
+}
+
+void launch_build_K(int n, int P, const double* d_C, const double* d_w, double* d_K, cudaStream_t st) {
+  const int64_t n3 = (int64_t)n * n * n;
+  int64_t blocks = (n3 * n3 + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  count_launch();
+  k_build_K<<<(unsigned)blocks, 256, 0, st>>>(n, P, d_C, d_w, d_K);
+}
+
+// Mode product on a tensor viewed as (I, n, Kd): out[i][a][k] = sum_m C[a][m] in[i][m][k].
+// If acc_w != 0, out = (first ? 0 : out) + acc_w * result.
+__global__ void k_mode(int64_t I, int n, int64_t Kd, const double* __restrict__ Cm, const double* __restrict__ in,
+                       double* __restrict__ out, double acc_w, int accumulate, int first) {
+  const int64_t total = I * n * Kd;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t % Kd;
+    const int a = (int)((t / Kd) % n);
+    const int64_t i = t / Kd / n;
+    const double* src = in + (size_t)i * n * Kd + k;
+    const double* c = Cm + (size_t)a * n;
+    double acc = 0.0;
+    for (int m = 0; m < n; ++m) acc += c[m] * src[(size_t)m * Kd];
+    if (accumulate)
+      out[t] = (first ? 0.0 : out[t]) + acc_w * acc;
+    else
+      out[t] = acc;
+  }
+}
+
+__global__ void k_axpy_w(int64_t count, const double* __restrict__ w, int p, const double* __restrict__ x,
+                         double* __restrict__ y, int first) {
+  const double wp = w[p];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    y[t] = (first ? 0.0 : y[t]) + wp * x[t];
+}
+
+static void launch_axpy_w(int64_t count, const double* w, int p, const double* x, double* y, int first, cudaStream_t st) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  count_launch();
+  k_axpy_w<<<(unsigned)blocks, 256, 0, st>>>(count, w, p, x, y, first);
+}
+
+void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const double* d_X, double* d_Y,
+                       int64_t ncol, double* d_t1, double* d_t2, cudaStream_t st) {
+  // X, Y: ncol rows of length n^3 (cube index (m1, m2, m3), m3 fastest).
+  const int64_t n3 = (int64_t)n * n * n;
+  const int64_t total = ncol * n3;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  const size_t nn = (size_t)n * n;
+  for (int p = 0; p < P; ++p) {
+    const double* cx = d_C + ((size_t)0 * P + p) * nn;
+    const double* cy = d_C + ((size_t)1 * P + p) * nn;
+    const double* cz = d_C + ((size_t)2 * P + p) * nn;
+    count_launch();
+    k_mode<<<(unsigned)blocks, 256, 0, st>>>(ncol, n, (int64_t)n * n, cx, d_X, d_t1, 0.0, 0, 0);
+    count_launch();
+    k_mode<<<(unsigned)blocks, 256, 0, st>>>(ncol * n, n, n, cy, d_t1, d_t2, 0.0, 0, 0);
+    // mode 3, then Y += w_p * result (the weight is read on the device)
+    count_launch();
+    k_mode<<<(unsigned)blocks, 256, 0, st>>>(ncol * nn, n, 1, cz, d_t2, d_t1, 0.0, 0, 0);
+    launch_axpy_w(total, d_w, p, d_t1, d_Y, p == 0, st);
+  }
+}
+
+// One block per unique pair r = (mu, nu); writes full rows mu*N_b+nu and nu*N_b+mu.
+__global__ void k_expand_B(int nbf, const double* __restrict__ Bu, int64_t ldu, double scale, double* __restrict__ B,
+                           int64_t ldB, const int* __restrict__ pair_mu, const int* __restrict__ pair_nu) {
+  const int64_t r = blockIdx.x;
+  const int mu = pair_mu[r], nu = pair_nu[r];
+  const double* src = Bu + (size_t)r * ldu;
+  double* row1 = B + ((size_t)mu * nbf + nu) * ldB;
+  double* row2 = B + ((size_t)nu * nbf + mu) * ldB;
+  const int64_t nc = (int64_t)nbf * nbf;
+  for (int64_t col = threadIdx.x; col < nc; col += blockDim.x) {
+    const int ka = (int)(col / nbf), la = (int)(col % nbf);
+    const double v = scale * src[pair_idx(nbf, ka, la)];
+    row1[col] = v;
+    if (mu != nu) row2[col] = v;
+  }
+}
+
+void launch_expand_B(const PairTable& t, int nbf, const double* d_Bu, int64_t ldu, double scale, double* d_B,
+                     int64_t ldB, cudaStream_t st) {
+  count_launch();
+  k_expand_B<<<(unsigned)t.npair, 256, 0, st>>>(nbf, d_Bu, ldu, scale, d_B, ldB, t.pair_mu, t.pair_nu);
+}
+
+// d_u[r][q] = D_q(mu, nu) * (mu == nu ? 1 : 2); D stored R x N_b x N_b.
+__global__ void k_pack_density(int nbf, int R, int64_t npair, const double* __restrict__ D, double* __restrict__ u) {
+  const int64_t total = npair * R;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % R);
+    const int64_t r = t / R;
+    // invert r -> (mu, nu): mu is the largest a with a*nbf - a(a-1)/2 <= r
+    int lo = 0, hi = nbf - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) / 2;
+      if ((int64_t)mid * nbf - (int64_t)mid * (mid - 1) / 2 <= r) lo = mid; else hi = mid - 1;
+    }
+    const int mu = lo;
+    const int nu = (int)(r - ((int64_t)mu * nbf - (int64_t)mu * (mu - 1) / 2)) + mu;
+    const double v = D[(size_t)q * nbf * nbf + (size_t)mu * nbf + nu];
+    u[t] = (mu == nu) ? v : 2.0 * v;
+  }
+}
+
+void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStream_t st) {
+  const int64_t npair = (int64_t)nbf * (nbf + 1) / 2;
+  int64_t blocks = (npair * R + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch();
+  k_pack_density<<<(unsigned)blocks, 256, 0, st>>>(nbf, R, npair, d_D, d_u);
+}
+
+// J_q(mu, nu) = J_q(nu, mu) = scale * Ju[r][q].
+__global__ void k_unpack_J(int nbf, int R, const double* __restrict__ Ju, double scale, double* __restrict__ J) {
+  const int64_t total = (int64_t)R * nbf * nbf;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / ((int64_t)nbf * nbf));
+    const int mu = (int)((t / nbf) % nbf), nu = (int)(t % nbf);
+    J[t] = scale * Ju[pair_idx(nbf, mu, nu) * R + q];
+  }
+}
+
+void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, cudaStream_t st) {
+  const int64_t total = (int64_t)R * nbf * nbf;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch();
+  k_unpack_J<<<(unsigned)blocks, 256, 0, st>>>(nbf, R, d_Ju, scale, d_J);
+}
+
+}  // namespace lrtei

@@ -1,0 +1,282 @@
+// k_setup.cu -- FP64 set-up kernels of a plan: Gauss-Legendre nodes (eq. TEI2, Proposition 3),
+// Chebyshev coefficient matrices (Definition 1, eq. chebcheb), basis normalisation, the
+// primitive-pair table (Proposition 1) and the 1D moment matrices S_d (eq. defV).
+//
+// All of this is FP64 on the device.  The moment integrals are computed by an 8-panel,
+// 32-point Gauss-Legendre rule over the window |x - P| <= 9/sqrt(p) of each primitive-pair
+// Gaussian, clipped to the box: one warp per (row, dimension), one lane per quadrature point.
+#include <math.h>
+
+#include "lrtei_internal.h"
+
+namespace lrtei {
+
+// ------------------------------------------------------------------ Gauss-Legendre ----
+// One thread per root.  Initial guess from Tricomi's asymptotic formula, Newton steps on the
+// Legendre polynomial (three-term recurrence), weight 2 (1 - x^2) / (N P_{N-1}(x))^2.
+__global__ void k_gauss_legendre(int N, double* z, double* w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double pi = 3.141592653589793238;
+  double th = pi * (4.0 * (i + 1) - 1.0) / (4.0 * N + 2.0);
+  double x = (1.0 - 1.0 / (8.0 * N * N) + 1.0 / (8.0 * N * N * N)) * cos(th);
+  double pn = 0.0, pm1 = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double a = 1.0, b = x;  // P_0, P_1
+    for (int k = 2; k <= N; ++k) {
+      double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+      a = b;
+      b = c;
+    }
+    pn = (N == 0) ? 1.0 : b;
+    pm1 = (N == 1) ? 1.0 : a;
+    double dpn = N * (pm1 - x * pn) / ((1.0 - x) * (1.0 + x));
+    double dx = pn / dpn;
+    x -= dx;
+    if (fabs(dx) <= 1e-16 * fabs(x) + 1e-300) break;
+  }
+  {
+    double a = 1.0, b = x;
+    for (int k = 2; k <= N; ++k) {
+      double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+      a = b;
+      b = c;
+    }
+    pm1 = (N == 1) ? 1.0 : a;
+  }
+  // roots come out in descending order of x; store ascending
+  z[N - 1 - i] = x;
+  w[N - 1 - i] = 2.0 * (1.0 - x) * (1.0 + x) / ((double)N * N * pm1 * pm1);
+}
+
+void launch_gauss_legendre(int N, double* d_z, double* d_w, cudaStream_t st) {
+  count_launch();
+  k_gauss_legendre<<<(N + 63) / 64, 64, 0, st>>>(N, d_z, d_w);
+}
+
+__global__ void k_nodes_map(int P, double omega, const double* z, double* s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) s[i] = 0.5 * omega * (1.0 + z[i]);
+}
+
+void launch_nodes_map(int P, double omega, const double* d_z, double* d_s, cudaStream_t st) {
+  count_launch();
+  k_nodes_map<<<(P + 127) / 128, 128, 0, st>>>(P, omega, d_z, d_s);
+}
+
+// ---------------------------------------------------------------- Chebyshev coefficients ----
+// One block per (d, p).  With Tm(a, k) = T_a(u_k) = cos(a (2k+1) pi / (2n)) and
+// F(k, k') = exp(-(s_p b_d)^2 (u_k - u_k')^2), alpha = (c_ab / n^2) (Tm F Tm^T)(a, b).
+__global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3, double* C) {
+  extern __shared__ double sm[];
+  double* Tm = sm;          // n x n
+  double* G = sm + n * n;   // n x n : G(k, b) = sum_k' F(k, k') Tm(b, k')
+  const int d = blockIdx.x / P, p = blockIdx.x % P;
+  const double pi = 3.141592653589793238;
+  const double sb = s[p] * half3[d];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int a = t / n, k = t % n;
+    Tm[t] = cos(a * (2.0 * k + 1.0) * pi / (2.0 * n));
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int k = t / n, b = t % n;
+    const double uk = cos((2.0 * k + 1.0) * pi / (2.0 * n));
+    double acc = 0.0;
+    for (int kk = 0; kk < n; ++kk) {
+      const double vk = cos((2.0 * kk + 1.0) * pi / (2.0 * n));
+      double df = sb * (uk - vk);
+      acc += exp(-df * df) * Tm[b * n + kk];
+    }
+    G[t] = acc;
+  }
+  __syncthreads();
+  double* out = C + (size_t)blockIdx.x * n * n;
+  const double inv = 1.0 / ((double)n * n);
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int a = t / n, b = t % n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc += Tm[a * n + k] * G[k * n + b];
+    double cab = (a == 0 ? 1.0 : 2.0) * (b == 0 ? 1.0 : 2.0);
+    out[t] = cab * inv * acc;
+  }
+}
+
+void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, double* d_C, cudaStream_t st) {
+  size_t smem = 2 * sizeof(double) * n * n;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launch();
+  k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_half3, d_C);
+}
+
+// ------------------------------------------------------------------ normalisation ----
+__device__ __forceinline__ double dfact_d(int k) {
+  double r = 1.0;
+  for (int i = k; i > 1; i -= 2) r *= i;
+  return r;
+}
+
+// One thread per basis function: primitive normalisation (2a/pi)^{3/4} (4a)^{L/2} / sqrt(prod
+// (2l_d - 1)!!) and contraction normalisation so that the contracted component has unit norm:
+// the overlap of two normalised primitives of one component is (2 sqrt(ab)/(a+b))^{L + 3/2}.
+__global__ void k_normalise(int nbf, const int* bf_shell, const int* bf_pow, const int* shell_nprim,
+                            const int* shell_poff, const double* exps, const double* coefs, const int* bf_coff,
+                            double* ncoef) {
+  int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= nbf) return;
+  const int sh = bf_shell[mu];
+  const int K = shell_nprim[sh], off = shell_poff[sh];
+  const int lx = bf_pow[3 * mu], ly = bf_pow[3 * mu + 1], lz = bf_pow[3 * mu + 2];
+  const int L = lx + ly + lz;
+  const double pi = 3.141592653589793238;
+  double denom = sqrt(dfact_d(2 * lx - 1) * dfact_d(2 * ly - 1) * dfact_d(2 * lz - 1));
+  double* out = ncoef + bf_coff[mu];
+  for (int k = 0; k < K; ++k) {
+    double a = exps[off + k];
+    out[k] = coefs[off + k] * pow(2.0 * a / pi, 0.75) * pow(4.0 * a, 0.5 * L) / denom;
+  }
+  double S = 0.0;
+  for (int k = 0; k < K; ++k)
+    for (int q = 0; q < K; ++q) {
+      double a = exps[off + k], b = exps[off + q];
+      double r = 2.0 * sqrt(a * b) / (a + b);
+      S += coefs[off + k] * coefs[off + q] * pow(r, L + 1.5);
+    }
+  // S is the self-overlap in units of normalised primitives; scale all coefficients.
+  double inv = 1.0 / sqrt(S);
+  for (int k = 0; k < K; ++k) out[k] *= inv;
+}
+
+void launch_normalise(int nbf, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
+                      const int* d_shell_poff, const double* d_exps, const double* d_coefs, const int* d_bf_coff,
+                      double* d_ncoef, cudaStream_t st) {
+  count_launch();
+  k_normalise<<<(nbf + 127) / 128, 128, 0, st>>>(nbf, d_bf_shell, d_bf_pow, d_shell_nprim, d_shell_poff, d_exps,
+                                                 d_coefs, d_bf_coff, d_ncoef);
+}
+
+// ------------------------------------------------------------------ pair table ----
+// One block per unique pair (mu <= nu); threads over its I_mu I_nu primitive pairs.
+// Gaussian product rule (Proposition 1): exp(-a(x-A)^2) exp(-b(x-B)^2) = K_AB exp(-p (x-P)^2).
+__global__ void k_pair_rows(int64_t npair, const int* pair_mu, const int* pair_nu, const int64_t* pair_row,
+                            const int* bf_shell, const int* bf_pow, const int* shell_nprim, const int* shell_poff,
+                            const double* shell_center, const double* exps, const int* bf_coff,
+                            const double* ncoef, int64_t nrows, int* row_pair, double* row_c, double* row_p,
+                            double* row_P, double* row_K, double* row_A, double* row_B, int8_t* row_pa,
+                            int8_t* row_pb) {
+  const int64_t r = blockIdx.x;
+  if (r >= npair) return;
+  const int mu = pair_mu[r], nu = pair_nu[r];
+  const int sm = bf_shell[mu], sn = bf_shell[nu];
+  const int Km = shell_nprim[sm], Kn = shell_nprim[sn];
+  const int64_t base = pair_row[r];
+  for (int j = threadIdx.x; j < Km * Kn; j += blockDim.x) {
+    const int j1 = j / Kn, j2 = j % Kn;
+    const int64_t row = base + j;
+    const double a = exps[shell_poff[sm] + j1], b = exps[shell_poff[sn] + j2];
+    const double p = a + b;
+    row_pair[row] = (int)r;
+    row_c[row] = ncoef[bf_coff[mu] + j1] * ncoef[bf_coff[nu] + j2];
+    row_p[row] = p;
+    for (int d = 0; d < 3; ++d) {
+      const double A = shell_center[3 * sm + d], B = shell_center[3 * sn + d];
+      row_P[d * nrows + row] = (a * A + b * B) / p;
+      row_K[d * nrows + row] = exp(-a * b / p * (A - B) * (A - B));
+      row_A[d * nrows + row] = A;
+      row_B[d * nrows + row] = B;
+      row_pa[d * nrows + row] = (int8_t)bf_pow[3 * mu + d];
+      row_pb[d * nrows + row] = (int8_t)bf_pow[3 * nu + d];
+    }
+  }
+}
+
+void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
+                      const int* d_shell_poff, const double* d_shell_center, const double* d_exps,
+                      const int* d_bf_coff, const double* d_ncoef, cudaStream_t st) {
+  count_launch();
+  k_pair_rows<<<(unsigned)t.npair, 64, 0, st>>>(t.npair, t.pair_mu, t.pair_nu, t.pair_row, d_bf_shell, d_bf_pow,
+                                                d_shell_nprim, d_shell_poff, d_shell_center, d_exps, d_bf_coff,
+                                                d_ncoef, t.nrows, t.row_pair, t.row_c, t.row_p, t.row_P, t.row_K,
+                                                t.row_A, t.row_B, t.row_pa, t.row_pb);
+}
+
+// ------------------------------------------------------------------ moments ----
+// S_d(row, m) = int_{lo_d}^{hi_d} (x-A)^i (x-B)^k K_AB exp(-p (x-P)^2) T_m((x - c_d)/h_d) dx.
+// One warp per (row, d); lane q holds quadrature point q of every panel and accumulates
+// f(x_q) w_q T_m(u_q) for all m in registers; a shared-memory transpose then sums over lanes.
+template <int NM>
+__global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const double* row_p, const double* row_P,
+                                                 const double* row_K, const double* row_A, const double* row_B,
+                                                 const int8_t* row_pa, const int8_t* row_pb, const double* lo3,
+                                                 const double* hi3, const double* gz, const double* gw, double* S) {
+  __shared__ double red[4][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * 4 + warp;  // (d, row) with row fastest
+  const bool active = item < 3 * nrows;
+  const int d = active ? (int)(item / nrows) : 0;
+  const int64_t row = active ? item % nrows : 0;
+  double acc[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) acc[m] = 0.0;
+  if (active) {
+    const double p = row_p[row];
+    const double Pc = row_P[d * nrows + row], K = row_K[d * nrows + row];
+    const double A = row_A[d * nrows + row], B = row_B[d * nrows + row];
+    const int ia = row_pa[d * nrows + row], ib = row_pb[d * nrows + row];
+    const double lo = lo3[d], hi = hi3[d];
+    const double cen = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+    const double reach = 9.0 / sqrt(p);
+    const double wl = fmax(lo, Pc - reach), wh = fmin(hi, Pc + reach);
+    if (wh > wl) {
+      const double hp = (wh - wl) / kMomentPanels;
+      const double zq = gz[lane], wq = gw[lane];
+      for (int pan = 0; pan < kMomentPanels; ++pan) {
+        const double mid = wl + (pan + 0.5) * hp;
+        const double x = mid + 0.5 * hp * zq;
+        const double dx = x - Pc;
+        double f = K * exp(-p * dx * dx) * (0.5 * hp * wq);
+        const double xa = x - A, xb = x - B;
+        for (int e = 0; e < ia; ++e) f *= xa;
+        for (int e = 0; e < ib; ++e) f *= xb;
+        const double u = (x - cen) / half;
+        double t0 = 1.0, t1 = u;
+        acc[0] += f;
+        if (NM > 1) acc[1] += f * u;
+#pragma unroll
+        for (int m = 2; m < NM; ++m) {
+          double t2 = 2.0 * u * t1 - t0;
+          acc[m] += f * t2;
+          t0 = t1;
+          t1 = t2;
+        }
+      }
+    }
+  }
+  // sum over lanes: 32 moments at a time through shared memory
+#pragma unroll
+  for (int m0 = 0; m0 < NM; m0 += 32) {
+#pragma unroll
+    for (int m = 0; m < 32; ++m)
+      if (m0 + m < NM) red[warp][lane][m] = acc[m0 + m];
+    __syncwarp();
+    double s = 0.0;
+    for (int l = 0; l < 32; ++l) s += red[warp][l][lane];
+    if (active && m0 + lane < n) S[((size_t)d * nrows + row) * n + m0 + lane] = s;
+    __syncwarp();
+  }
+}
+
+void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const double* d_gz,
+                    const double* d_gw, double* d_S, cudaStream_t st) {
+  const int64_t items = 3 * t.nrows;
+  const unsigned blocks = (unsigned)((items + 3) / 4);
+  count_launch();
+  if (n <= 32)
+    k_moments<32><<<blocks, 128, 0, st>>>(t.nrows, n, t.row_p, t.row_P, t.row_K, t.row_A, t.row_B, t.row_pa,
+                                          t.row_pb, d_lo3, d_hi3, d_gz, d_gw, d_S);
+  else
+    k_moments<64><<<blocks, 128, 0, st>>>(t.nrows, n, t.row_p, t.row_P, t.row_K, t.row_A, t.row_B, t.row_pa,
+                                          t.row_pb, d_lo3, d_hi3, d_gz, d_gw, d_S);
+}
+
+}  // namespace lrtei

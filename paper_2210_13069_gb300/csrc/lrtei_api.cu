@@ -1,0 +1,600 @@
+// lrtei_api.cu -- the C ABI of include/lrtei.h: basis and plan objects, host-side validation,
+// workspace management and the orchestration of the device kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lrtei_internal.h"
+
+namespace lrtei {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+lrtei_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return LRTEI_ERR_CUDA;
+}
+
+lrtei_status finish_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return LRTEI_OK;
+}
+
+}  // namespace lrtei
+
+using namespace lrtei;
+
+struct lrtei_basis {
+  int nshells = 0, nbf = 0;
+  std::vector<double> centers, exps, coefs;
+  std::vector<int> l, nprim, poff;
+  std::vector<int> bf_shell, bf_pow, bf_coff;
+  int ncoef = 0;
+  double amin = 0.0;
+};
+
+struct lrtei_plan {
+  lrtei_basis basis;
+  double omega = 0.0;
+  int n = 0, P = 0;
+  double lo[3], hi[3];
+  lrtei_precision prec = LRTEI_FP64;
+  int last_form = 0;
+  PairTable t;
+  // device data
+  int *d_bf_shell = nullptr, *d_bf_pow = nullptr, *d_shell_nprim = nullptr, *d_shell_poff = nullptr,
+      *d_bf_coff = nullptr;
+  double *d_shell_center = nullptr, *d_exps = nullptr, *d_coefs = nullptr, *d_ncoef = nullptr;
+  double *d_z = nullptr, *d_s = nullptr, *d_w = nullptr, *d_gz = nullptr, *d_gw = nullptr;
+  double *d_lo3 = nullptr, *d_hi3 = nullptr, *d_half3 = nullptr;
+  double *d_C = nullptr, *d_S = nullptr;
+  int* d_status = nullptr;
+  // lazily built
+  double* d_T = nullptr;      // Hadamard: 3 * P * nrows * n
+  double* d_F = nullptr;      // factored: npair * n^3 (FP64)
+  float* d_F32 = nullptr;     // factored: npair * n^3 (FP32)
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+
+  template <typename T>
+  lrtei_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    size_t b = count * sizeof(T);
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
+      return LRTEI_ERR_ALLOC;
+    }
+    allocs.push_back(q);
+    bytes += b;
+    *p = (T*)q;
+    return LRTEI_OK;
+  }
+  void release(void* q, size_t b) {
+    if (!q) return;
+    auto it = std::find(allocs.begin(), allocs.end(), q);
+    if (it != allocs.end()) {
+      allocs.erase(it);
+      cudaFree(q);
+      bytes -= b;
+    }
+  }
+  ~lrtei_plan() {
+    for (void* q : allocs) cudaFree(q);
+  }
+};
+
+#define LRTEI_TRY(expr)                    \
+  do {                                     \
+    lrtei_status s__ = (expr);             \
+    if (s__ != LRTEI_OK) return s__;       \
+  } while (0)
+
+static inline int64_t npair_of(int nbf) { return (int64_t)nbf * (nbf + 1) / 2; }
+
+extern "C" {
+
+const char* lrtei_last_error(void) { return g_err.c_str(); }
+const char* lrtei_version(void) { return "lrtei 0.1 (sm_103a)"; }
+
+lrtei_status lrtei_basis_create(int nshells, const double* centers, const int* l, const int* nprim,
+                                const double* exps, const double* coefs, lrtei_basis** out) {
+  if (!out) { set_error("out is NULL"); return LRTEI_ERR_ARG; }
+  *out = nullptr;
+  if (nshells <= 0 || !centers || !l || !nprim || !exps || !coefs) {
+    set_error("invalid basis arguments (nshells=%d)", nshells);
+    return LRTEI_ERR_ARG;
+  }
+  lrtei_basis* b = new lrtei_basis();
+  b->nshells = nshells;
+  int np = 0;
+  for (int s = 0; s < nshells; ++s) {
+    if (l[s] < 0 || l[s] > 4 || nprim[s] < 1 || nprim[s] > 16) {
+      set_error("shell %d: l=%d nprim=%d out of range (l in 0..4, nprim in 1..16)", s, l[s], nprim[s]);
+      delete b;
+      return LRTEI_ERR_ARG;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (!isfinite(centers[3 * s + d])) { set_error("shell %d: non-finite centre", s); delete b; return LRTEI_ERR_ARG; }
+    b->poff.push_back(np);
+    np += nprim[s];
+  }
+  b->amin = 1e300;
+  for (int k = 0; k < np; ++k) {
+    if (!(exps[k] > 0.0) || !isfinite(exps[k]) || !isfinite(coefs[k])) {
+      set_error("primitive %d: exponent must be > 0 and finite, coefficient finite", k);
+      delete b;
+      return LRTEI_ERR_ARG;
+    }
+    b->amin = std::min(b->amin, exps[k]);
+  }
+  b->centers.assign(centers, centers + 3 * nshells);
+  b->l.assign(l, l + nshells);
+  b->nprim.assign(nprim, nprim + nshells);
+  b->exps.assign(exps, exps + np);
+  b->coefs.assign(coefs, coefs + np);
+  // Cartesian expansion: lx = l..0, ly = l-lx..0, lz = l-lx-ly
+  for (int s = 0; s < nshells; ++s)
+    for (int lx = l[s]; lx >= 0; --lx)
+      for (int ly = l[s] - lx; ly >= 0; --ly) {
+        b->bf_shell.push_back(s);
+        b->bf_pow.push_back(lx);
+        b->bf_pow.push_back(ly);
+        b->bf_pow.push_back(l[s] - lx - ly);
+        b->bf_coff.push_back(b->ncoef);
+        b->ncoef += nprim[s];
+      }
+  b->nbf = (int)b->bf_shell.size();
+  *out = b;
+  return LRTEI_OK;
+}
+
+void lrtei_basis_destroy(lrtei_basis* basis) { delete basis; }
+int lrtei_basis_nbf(const lrtei_basis* basis) { return basis ? basis->nbf : 0; }
+
+lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
+                               const double* box_hi, lrtei_precision precision, void* stream, lrtei_plan** out) {
+  if (!out) { set_error("out is NULL"); return LRTEI_ERR_ARG; }
+  *out = nullptr;
+  if (!basis) { set_error("basis is NULL"); return LRTEI_ERR_ARG; }
+  if (!(omega > 0.0) || !isfinite(omega)) { set_error("omega must be > 0 (got %g)", omega); return LRTEI_ERR_ARG; }
+  if (n < 1 || n > kMaxN) { set_error("n must be in 1..%d (got %d)", kMaxN, n); return LRTEI_ERR_ARG; }
+  if (P < 1 || P > kMaxP) { set_error("P must be in 1..%d (got %d)", kMaxP, P); return LRTEI_ERR_ARG; }
+  if ((box_lo == nullptr) != (box_hi == nullptr)) { set_error("box_lo and box_hi must both be given or both NULL"); return LRTEI_ERR_ARG; }
+  if (precision < LRTEI_FP64 || precision > LRTEI_BF16) { set_error("unknown precision %d", (int)precision); return LRTEI_ERR_ARG; }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    set_error("no CUDA device available (%s)", cudaGetErrorString(ce));
+    return LRTEI_ERR_CUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  lrtei_plan* pl = new lrtei_plan();
+  pl->basis = *basis;
+  pl->omega = omega;
+  pl->n = n;
+  pl->P = P;
+  pl->prec = precision;
+  const lrtei_basis& b = pl->basis;
+  // box (eq. compact)
+  if (box_lo) {
+    for (int d = 0; d < 3; ++d) {
+      if (!(box_hi[d] > box_lo[d]) || !isfinite(box_lo[d]) || !isfinite(box_hi[d])) {
+        set_error("box: hi[%d] must exceed lo[%d]", d, d);
+        delete pl;
+        return LRTEI_ERR_ARG;
+      }
+      pl->lo[d] = box_lo[d];
+      pl->hi[d] = box_hi[d];
+    }
+  } else {
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int s = 0; s < b.nshells; ++s)
+      for (int d = 0; d < 3; ++d) {
+        mn[d] = std::min(mn[d], b.centers[3 * s + d]);
+        mx[d] = std::max(mx[d], b.centers[3 * s + d]);
+      }
+    const double margin = sqrt(log(1e16) / (2.0 * b.amin));
+    double half = 0.0;
+    for (int d = 0; d < 3; ++d) half = std::max(half, 0.5 * (mx[d] - mn[d]) + margin);
+    for (int d = 0; d < 3; ++d) {
+      const double c = 0.5 * (mn[d] + mx[d]);
+      pl->lo[d] = c - half;
+      pl->hi[d] = c + half;
+    }
+  }
+  // pair table structure (host integer bookkeeping)
+  const int nbf = b.nbf;
+  PairTable& t = pl->t;
+  t.npair = npair_of(nbf);
+  std::vector<int> pmu(t.npair), pnu(t.npair), pI(t.npair);
+  std::vector<int64_t> prow(t.npair + 1);
+  int64_t r = 0, rows = 0;
+  for (int mu = 0; mu < nbf; ++mu)
+    for (int nu = mu; nu < nbf; ++nu) {
+      pmu[r] = mu;
+      pnu[r] = nu;
+      pI[r] = b.nprim[b.bf_shell[mu]] * b.nprim[b.bf_shell[nu]];
+      prow[r] = rows;
+      rows += pI[r];
+      ++r;
+    }
+  prow[t.npair] = rows;
+  t.nrows = rows;
+
+  lrtei_status s;
+#define PA(ptr, cnt)                           \
+  if ((s = pl->alloc(&(ptr), (cnt))) != LRTEI_OK) { delete pl; return s; }
+  PA(pl->d_bf_shell, nbf);
+  PA(pl->d_bf_pow, 3 * nbf);
+  PA(pl->d_bf_coff, nbf);
+  PA(pl->d_shell_nprim, b.nshells);
+  PA(pl->d_shell_poff, b.nshells);
+  PA(pl->d_shell_center, 3 * b.nshells);
+  PA(pl->d_exps, b.exps.size());
+  PA(pl->d_coefs, b.coefs.size());
+  PA(pl->d_ncoef, b.ncoef);
+  PA(pl->d_z, P);
+  PA(pl->d_s, P);
+  PA(pl->d_w, P);
+  PA(pl->d_gz, kMomentPts);
+  PA(pl->d_gw, kMomentPts);
+  PA(pl->d_lo3, 3);
+  PA(pl->d_hi3, 3);
+  PA(pl->d_half3, 3);
+  PA(pl->d_C, (size_t)3 * P * n * n);
+  PA(pl->d_S, (size_t)3 * t.nrows * n);
+  PA(pl->d_status, 1);
+  PA(t.pair_mu, t.npair);
+  PA(t.pair_nu, t.npair);
+  PA(t.pair_row, t.npair + 1);
+  PA(t.pair_I, t.npair);
+  PA(t.row_pair, t.nrows);
+  PA(t.row_c, t.nrows);
+  PA(t.row_p, t.nrows);
+  PA(t.row_P, 3 * t.nrows);
+  PA(t.row_K, 3 * t.nrows);
+  PA(t.row_A, 3 * t.nrows);
+  PA(t.row_B, 3 * t.nrows);
+  PA(t.row_pa, 3 * t.nrows);
+  PA(t.row_pb, 3 * t.nrows);
+#undef PA
+  double half3[3];
+  for (int d = 0; d < 3; ++d) half3[d] = 0.5 * (pl->hi[d] - pl->lo[d]);
+#define UP(dst, src, cnt)                                                                                 \
+  if ((ce = cudaMemcpyAsync((dst), (src), sizeof(*(src)) * (cnt), cudaMemcpyHostToDevice, st)) != cudaSuccess) { \
+    delete pl;                                                                                            \
+    return cuda_fail(ce, "upload " #dst);                                                                 \
+  }
+  UP(pl->d_bf_shell, b.bf_shell.data(), nbf);
+  UP(pl->d_bf_pow, b.bf_pow.data(), 3 * nbf);
+  UP(pl->d_bf_coff, b.bf_coff.data(), nbf);
+  UP(pl->d_shell_nprim, b.nprim.data(), b.nshells);
+  UP(pl->d_shell_poff, b.poff.data(), b.nshells);
+  UP(pl->d_shell_center, b.centers.data(), 3 * b.nshells);
+  UP(pl->d_exps, b.exps.data(), b.exps.size());
+  UP(pl->d_coefs, b.coefs.data(), b.coefs.size());
+  UP(pl->d_lo3, pl->lo, 3);
+  UP(pl->d_hi3, pl->hi, 3);
+  UP(pl->d_half3, half3, 3);
+  UP(t.pair_mu, pmu.data(), t.npair);
+  UP(t.pair_nu, pnu.data(), t.npair);
+  UP(t.pair_row, prow.data(), t.npair + 1);
+  UP(t.pair_I, pI.data(), t.npair);
+#undef UP
+  // The uploads above are from pageable memory: they complete (staged) before returning.
+  ce = cudaMemsetAsync(pl->d_status, 0, sizeof(int), st);
+  if (ce != cudaSuccess) { delete pl; return cuda_fail(ce, "status reset"); }
+  launch_normalise(nbf, pl->d_bf_shell, pl->d_bf_pow, pl->d_shell_nprim, pl->d_shell_poff, pl->d_exps, pl->d_coefs,
+                   pl->d_bf_coff, pl->d_ncoef, st);
+  launch_pair_rows(t, pl->d_bf_shell, pl->d_bf_pow, pl->d_shell_nprim, pl->d_shell_poff, pl->d_shell_center,
+                   pl->d_exps, pl->d_bf_coff, pl->d_ncoef, st);
+  launch_gauss_legendre(P, pl->d_z, pl->d_w, st);
+  launch_nodes_map(P, omega, pl->d_z, pl->d_s, st);
+  launch_gauss_legendre(kMomentPts, pl->d_gz, pl->d_gw, st);
+  launch_cheb_coeff(n, P, pl->d_s, pl->d_half3, pl->d_C, st);
+  {
+    ProfScope ps("moments", st);
+    launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_gz, pl->d_gw, pl->d_S, st);
+  }
+  if ((s = finish_launch("plan set-up kernels")) != LRTEI_OK) { delete pl; return s; }
+  *out = pl;
+  return LRTEI_OK;
+}
+
+void lrtei_plan_destroy(lrtei_plan* plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  delete plan;
+}
+
+lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info) {
+  if (!plan || !info) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  info->nbf = plan->basis.nbf;
+  info->npair = plan->t.npair;
+  info->nrows = plan->t.nrows;
+  info->n = plan->n;
+  info->P = plan->P;
+  info->omega = plan->omega;
+  for (int d = 0; d < 3; ++d) { info->box_lo[d] = plan->lo[d]; info->box_hi[d] = plan->hi[d]; }
+  info->precision = plan->prec;
+  info->last_form = plan->last_form;
+  info->workspace_bytes = plan->bytes;
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_plan_status(lrtei_plan* plan) {
+  if (!plan) { set_error("plan is NULL"); return LRTEI_ERR_ARG; }
+  LRTEI_CUDA(cudaDeviceSynchronize());
+  int h = 0;
+  LRTEI_CUDA(cudaMemcpy(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  LRTEI_CUDA(cudaMemset(plan->d_status, 0, sizeof(int)));
+  if (h == kDevTimeout) { set_error("a device-side bounded wait gave up"); return LRTEI_ERR_TIMEOUT; }
+  if (h == kDevNonFinite) { set_error("non-finite value detected on the device"); return LRTEI_ERR_NUMERIC; }
+  return LRTEI_OK;
+}
+
+}  // extern "C"
+
+namespace lrtei {
+__global__ void k_scale_copy_rows(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
+                                  double scale) {
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / cols, j = t % cols;
+    dst[i * ldd + j] = scale * src[i * lds + j];
+  }
+}
+}  // namespace lrtei
+
+static void scale_copy_rows(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
+                     double scale, cudaStream_t st) {
+  int64_t b = (rows * cols + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (rows * cols > 0) count_launch();
+  if (rows * cols > 0) lrtei::k_scale_copy_rows<<<(unsigned)b, 256, 0, st>>>(src, lds, dst, ldd, rows, cols, scale);
+}
+
+// ------------------------------------------------------------------ internals of the forms
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+lrtei_status ensure_T(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->d_T) return LRTEI_OK;
+  LRTEI_TRY(pl->alloc(&pl->d_T, (size_t)3 * pl->P * pl->t.nrows * pl->n));
+  launch_tmat(pl->t.nrows, pl->n, pl->P, pl->d_S, pl->d_C, pl->d_T, st);
+  return finish_launch("tmat");
+}
+
+lrtei_status ensure_F64(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->d_F) return LRTEI_OK;
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
+  LRTEI_TRY(pl->alloc(&pl->d_F, (size_t)pl->t.npair * n3));
+  {
+    ProfScope ps("build_F", st);
+    launch_build_F<double>(pl->t, pl->n, pl->d_S, 0, pl->t.npair, pl->d_F, n3, st);
+  }
+  return finish_launch("build_F");
+}
+
+lrtei_status ensure_F32(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->d_F32) return LRTEI_OK;
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
+  LRTEI_TRY(pl->alloc(&pl->d_F32, (size_t)pl->t.npair * n3));
+  launch_build_F<float>(pl->t, pl->n, pl->d_S, 0, pl->t.npair, pl->d_F32, n3, st);
+  return finish_launch("build_F32");
+}
+
+// Scratch buffer owned by the call (freed at the end of the call, stream-ordered).
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaStream_t st;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  template <typename T>
+  lrtei_status get(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(16, count * sizeof(T)), st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("scratch allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return LRTEI_ERR_ALLOC;
+    }
+    ptrs.push_back(q);
+    *p = (T*)q;
+    return LRTEI_OK;
+  }
+  ~Scratch() {
+    for (void* q : ptrs) cudaFreeAsync(q, st);
+  }
+};
+
+int choose_form(const lrtei_plan* pl, lrtei_form form) {
+  if (form == LRTEI_FORM_HADAMARD || form == LRTEI_FORM_FACTORED) return form;
+  // Hadamard: ~ npair^2 * P * Ibar^2 * (6n + 3); factored: ~ npair^2 n^3 + 6 P n^4 npair.
+  const double Ibar2 = (double)pl->t.nrows / pl->t.npair;
+  const double had = (double)pl->P * Ibar2 * Ibar2 * (6.0 * pl->n + 3.0);
+  const double fac = (double)pl->n * pl->n * pl->n * 2.0;
+  return had <= fac ? LRTEI_FORM_HADAMARD : LRTEI_FORM_FACTORED;
+}
+
+// Rows [r0, r1) of B_u (full width npair) into out (ld), prefactor included.
+lrtei_status bu_rows(lrtei_plan* pl, int form, int64_t r0, int64_t r1, double* out, int64_t ld, cudaStream_t st) {
+  const double pref = pl->omega / sqrt(kPi);
+  const int n = pl->n, P = pl->P;
+  const int64_t npair = pl->t.npair, n3 = (int64_t)n * n * n, nr = r1 - r0;
+  if (nr <= 0) return LRTEI_OK;
+  if (form == LRTEI_FORM_HADAMARD) {
+    LRTEI_TRY(ensure_T(pl, st));
+    {
+      ProfScope ps("hadamard", st);
+      launch_hadamard_rows(pl->t, n, P, pl->d_S, pl->d_T, pl->d_w, pref, r0, r1, out, ld, st);
+    }
+    return finish_launch("hadamard_rows");
+  }
+  // factored: G = kron(F rows), B_u rows = pref * G F^T
+  LRTEI_TRY(ensure_F64(pl, st));
+  Scratch sc(st);
+  double *G, *t1, *t2;
+  LRTEI_TRY(sc.get(&G, (size_t)nr * n3));
+  LRTEI_TRY(sc.get(&t1, (size_t)nr * n3));
+  LRTEI_TRY(sc.get(&t2, (size_t)nr * n3));
+  {
+    ProfScope ps("kron", st);
+    launch_kron_apply(n, P, pl->d_C, pl->d_w, pl->d_F + r0 * n3, G, nr, t1, t2, st);
+  }
+  if (pl->prec == LRTEI_FP32) {
+    LRTEI_TRY(ensure_F32(pl, st));
+    float *G32, *B32;
+    LRTEI_TRY(sc.get(&G32, (size_t)nr * n3));
+    LRTEI_TRY(sc.get(&B32, (size_t)nr * npair));
+    convert_f64_to_f32(G, G32, nr * n3, st);
+    {
+      ProfScope ps("gemm_fp32", st);
+      gemm_cuda_core<float>(false, true, nr, npair, n3, 1.0f, G32, n3, pl->d_F32, n3, 0.0f, B32, npair, st);
+    }
+    double* tmp;
+    LRTEI_TRY(sc.get(&tmp, (size_t)nr * npair));
+    convert_f32_to_f64(B32, tmp, nr * npair, st);
+    scale_copy_rows(tmp, npair, out, ld, nr, npair, pref, st);
+    return finish_launch("fp32 B rows");
+  }
+  {
+    ProfScope ps("gemm_fp64", st);
+    gemm_cuda_core<double>(false, true, nr, npair, n3, pref, G, n3, pl->d_F, n3, 0.0, out, ld, st);
+  }
+  return finish_launch("factored B rows");
+}
+
+}  // namespace
+
+extern "C" {
+
+lrtei_status lrtei_assemble_Bu_rows(lrtei_plan* plan, lrtei_form form, int64_t row_begin, int64_t row_end,
+                                    double* d_Bu, int64_t ld, void* stream) {
+  if (!plan || !d_Bu) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (row_begin < 0 || row_end > plan->t.npair || row_begin > row_end) {
+    set_error("row range [%lld, %lld) outside [0, %lld)", (long long)row_begin, (long long)row_end,
+              (long long)plan->t.npair);
+    return LRTEI_ERR_ARG;
+  }
+  if (ld < plan->t.npair) { set_error("ld %lld < npair %lld", (long long)ld, (long long)plan->t.npair); return LRTEI_ERR_ARG; }
+  const int f = choose_form(plan, form);
+  plan->last_form = f;
+  return bu_rows(plan, f, row_begin, row_end, d_Bu, ld, (cudaStream_t)stream);
+}
+
+lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, int64_t ld, void* stream) {
+  if (!plan || !d_B) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  const int nbf = plan->basis.nbf;
+  const int64_t nb2 = (int64_t)nbf * nbf, npair = plan->t.npair;
+  if (ld < nb2) { set_error("ld %lld < N_b^2 = %lld", (long long)ld, (long long)nb2); return LRTEI_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int f = choose_form(plan, form);
+  plan->last_form = f;
+  // process B_u in row blocks of at most ~1 GiB
+  int64_t rb = std::max<int64_t>(1, (int64_t)((1ULL << 30) / (sizeof(double) * (size_t)npair)));
+  if (f == LRTEI_FORM_FACTORED) {
+    const int64_t n3 = (int64_t)plan->n * plan->n * plan->n;
+    rb = std::max<int64_t>(1, std::min<int64_t>(rb, (int64_t)((1ULL << 30) / (sizeof(double) * 3 * (size_t)n3))));
+  }
+  rb = std::min(rb, npair);
+  Scratch sc(st);
+  double* blk;
+  LRTEI_TRY(sc.get(&blk, (size_t)rb * npair));
+  for (int64_t r0 = 0; r0 < npair; r0 += rb) {
+    const int64_t r1 = std::min(npair, r0 + rb);
+    LRTEI_TRY(bu_rows(plan, f, r0, r1, blk, npair, st));
+    PairTable sub = plan->t;
+    sub.pair_mu += r0;
+    sub.pair_nu += r0;
+    sub.npair = r1 - r0;
+    {
+      ProfScope ps("expand_B", st);
+      launch_expand_B(sub, nbf, blk, npair, 1.0, d_B, ld, st);
+    }
+    LRTEI_TRY(finish_launch("expand_B"));
+  }
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out, void* stream) {
+  if (!plan) { set_error("plan is NULL"); return LRTEI_ERR_ARG; }
+  if (count < 0 || (count > 0 && (!d_idx4 || !d_out))) { set_error("invalid entries arguments"); return LRTEI_ERR_ARG; }
+  if (count == 0) return LRTEI_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  LRTEI_TRY(ensure_T(plan, st));
+  Scratch sc(st);
+  int64_t *r, *c;
+  LRTEI_TRY(sc.get(&r, count));
+  LRTEI_TRY(sc.get(&c, count));
+  launch_idx4_to_pairs(plan->basis.nbf, d_idx4, count, r, c, st);
+  launch_hadamard_pairs(plan->t, plan->n, plan->P, plan->d_S, plan->d_T, plan->d_w, plan->omega / sqrt(kPi), r, c,
+                        count, d_out, st);
+  return finish_launch("entries");
+}
+
+lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d_s, double* d_w, double* d_c,
+                           void* stream) {
+  if (!plan) { set_error("plan is NULL"); return LRTEI_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = plan->n, P = plan->P, nrows = plan->t.nrows;
+  if (d_S) LRTEI_CUDA(cudaMemcpyAsync(d_S, plan->d_S, sizeof(double) * 3 * nrows * n, cudaMemcpyDeviceToDevice, st));
+  if (d_C) LRTEI_CUDA(cudaMemcpyAsync(d_C, plan->d_C, sizeof(double) * 3 * P * n * n, cudaMemcpyDeviceToDevice, st));
+  if (d_s) LRTEI_CUDA(cudaMemcpyAsync(d_s, plan->d_s, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+  if (d_w) LRTEI_CUDA(cudaMemcpyAsync(d_w, plan->d_w, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+  if (d_c) LRTEI_CUDA(cudaMemcpyAsync(d_c, plan->t.row_c, sizeof(double) * nrows, cudaMemcpyDeviceToDevice, st));
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream) {
+  if (!plan || !d_D || !d_J) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (R <= 0) { set_error("R must be positive (got %d)", R); return LRTEI_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nbf = plan->basis.nbf, n = plan->n, P = plan->P;
+  const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;
+  const double pref = plan->omega / sqrt(kPi);
+  Scratch sc(st);
+  double *Du, *Xt, *Yt, *t1, *t2, *Ju;
+  LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&Xt, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Yt, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t1, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t2, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Ju, (size_t)npair * R));
+  launch_pack_density(nbf, R, d_D, Du, st);
+  LRTEI_TRY(ensure_F64(plan, st));
+  // Xt = Du^T F  (R x n^3); Yt = kron(Xt); Ju = F Yt^T (npair x R)
+  gemm_cuda_core<double>(true, false, R, n3, npair, 1.0, Du, R, plan->d_F, n3, 0.0, Xt, n3, st);
+  launch_kron_apply(n, P, plan->d_C, plan->d_w, Xt, Yt, R, t1, t2, st);
+  gemm_cuda_core<double>(false, true, npair, R, n3, 1.0, plan->d_F, n3, Yt, n3, 0.0, Ju, R, st);
+  launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+  return finish_launch("jbuild");
+}
+
+lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,
+                                  double* const* d_J, void* stream) {
+  if (!plans || nmol <= 0 || !d_D || !R || !d_J) { set_error("invalid batched arguments"); return LRTEI_ERR_ARG; }
+  for (int m = 0; m < nmol; ++m) LRTEI_TRY(lrtei_jbuild(plans[m], d_D[m], R[m], d_J[m], stream));
+  return LRTEI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// lrtei_internal.h -- internal declarations shared by the CUDA translation units of liblrtei.
+// Not part of the C ABI (include/lrtei.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lrtei.h"
+
+namespace lrtei {
+
+constexpr int kMaxN = 64;        // Chebyshev nodes per dimension
+constexpr int kMaxP = 128;       // Gauss-Legendre nodes over [0, omega]
+constexpr int kMomentPanels = 8; // panels of the device moment quadrature
+constexpr int kMomentPts = 32;   // Gauss-Legendre points per panel (one per lane)
+
+// Device-side status word (latched by kernels, read by lrtei_plan_status).
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevNonFinite = 2 };
+
+void set_error(const char* fmt, ...);
+lrtei_status cuda_fail(cudaError_t e, const char* what);
+
+#define LRTEI_CUDA(call)                                  \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+// Counts kernel launches made by the library (reported by lrtei_profile_get("*")).
+void count_launch();
+
+// Kernel timing: events recorded on the launching stream when profiling is enabled.
+struct ProfScope {
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(const char* n, cudaStream_t s);
+  ~ProfScope();
+};
+
+// Pair / row table on the device (structure of arrays; rows are primitive pairs of unique
+// basis pairs mu <= nu, grouped by pair).
+struct PairTable {
+  int64_t npair = 0, nrows = 0;
+  int* pair_mu = nullptr;      // [npair]
+  int* pair_nu = nullptr;      // [npair]
+  int64_t* pair_row = nullptr; // [npair + 1] first row of each pair
+  int* pair_I = nullptr;       // [npair] rows of each pair (I_mu I_nu)
+  // per row
+  int* row_pair = nullptr;     // [nrows]
+  double* row_c = nullptr;     // [nrows] c_j = c_{j1} c_{j2} (normalised)
+  double* row_p = nullptr;     // [nrows] a + b
+  double* row_P = nullptr;     // [3 * nrows] product centre (d-major)
+  double* row_K = nullptr;     // [3 * nrows] exp(-ab/p (A_d - B_d)^2)
+  double* row_A = nullptr;     // [3 * nrows] centre of mu
+  double* row_B = nullptr;     // [3 * nrows] centre of nu
+  int8_t* row_pa = nullptr;    // [3 * nrows] power of mu in d
+  int8_t* row_pb = nullptr;    // [3 * nrows] power of nu in d
+};
+
+// ---------------------------------------------------------------- setup kernels
+// Gauss-Legendre nodes/weights on [-1, 1] for N points (device, one thread per root).
+void launch_gauss_legendre(int N, double* d_z, double* d_w, cudaStream_t st);
+// s_p = omega (1 + z_p) / 2.
+void launch_nodes_map(int P, double omega, const double* d_z, double* d_s, cudaStream_t st);
+// C[d][p] = Chebyshev coefficients of exp(-s_p^2 half_d^2 (u - v)^2), n x n.
+void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, double* d_C, cudaStream_t st);
+// Normalised coefficients per (basis function, primitive).
+void launch_normalise(int nbf, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
+                      const int* d_shell_poff, const double* d_exps, const double* d_coefs, const int* d_bf_coff,
+                      double* d_ncoef, cudaStream_t st);
+// Fill the per-row part of the pair table.
+void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
+                      const int* d_shell_poff, const double* d_shell_center, const double* d_exps,
+                      const int* d_bf_coff, const double* d_ncoef, cudaStream_t st);
+// S[d][row][m] for m < n, FP64.  d_gz/d_gw: kMomentPts Gauss-Legendre rule on [-1,1].
+void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const double* d_gz,
+                    const double* d_gw, double* d_S, cudaStream_t st);
+
+// ---------------------------------------------------------------- Hadamard form (FP64)
+// T[d][p][row][b] = sum_a S[d][row][a] C[d][p][a][b]
+void launch_tmat(int64_t nrows, int n, int P, const double* d_S, const double* d_C, double* d_T, cudaStream_t st);
+// Entries by Algorithm 1 on unique pairs: out[e] = B_u(r_e, c_e), prefactor included.
+void launch_hadamard_pairs(const PairTable& t, int n, int P, const double* d_S, const double* d_T,
+                           const double* d_w, double pref, const int64_t* d_r, const int64_t* d_c, int64_t count,
+                           double* d_out, cudaStream_t st);
+// Block of B_u rows [r0, r1) x all columns, Hadamard form.
+void launch_hadamard_rows(const PairTable& t, int n, int P, const double* d_S, const double* d_T, const double* d_w,
+                          double pref, int64_t r0, int64_t r1, double* d_Bu, int64_t ld, cudaStream_t st);
+// (mu,nu,ka,la) quadruples -> unique pair indices.
+void launch_idx4_to_pairs(int nbf, const int32_t* d_idx4, int64_t count, int64_t* d_r, int64_t* d_c,
+                          cudaStream_t st);
+
+// ---------------------------------------------------------------- factored form
+// F_u[r][m] = sum_{j in r} c_j S_x(j,m1) S_y(j,m2) S_z(j,m3), m = (m1 n + m2) n + m3, for r in [r0, r1).
+template <typename T>
+void launch_build_F(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, T* d_F, int64_t ldF,
+                    cudaStream_t st);
+// Dense K = sum_p w_p C_x^p (x) C_y^p (x) C_z^p  (n^3 x n^3), FP64.
+void launch_build_K(int n, int P, const double* d_C, const double* d_w, double* d_K, cudaStream_t st);
+// Y = sum_p w_p (C_x^p (x) C_y^p (x) C_z^p) X, X/Y: n^3 x ncol (column index fastest).
+void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const double* d_X, double* d_Y,
+                       int64_t ncol, double* d_t1, double* d_t2, cudaStream_t st);
+// Expand the unique-pair square B_u (npair x npair, ld) into full B (N_b^2 x N_b^2, ldB), times scale.
+void launch_expand_B(const PairTable& t, int nbf, const double* d_Bu, int64_t ldu, double scale, double* d_B,
+                     int64_t ldB, cudaStream_t st);
+// Densities -> unique-pair vectors: d_u[r][q] = D_q(mu,nu) * (mu == nu ? 1 : 2).
+void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStream_t st);
+// Unique-pair results -> full symmetric J: J_q(mu,nu) = J_q(nu,mu) = scale * Ju[r][q].
+void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, cudaStream_t st);
+
+// ---------------------------------------------------------------- CUDA-core GEMM
+// C[M x N] = alpha * op(A) op(B) + beta * C, row-major; transA: A is K x M; transB: B is N x K.
+template <typename T>
+void gemm_cuda_core(bool transA, bool transB, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
+                    const T* B, int64_t ldb, T beta, T* C, int64_t ldc, cudaStream_t st);
+void convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_t st);
+void convert_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor cores (tcgen05)
+struct SplitMatrix {  // row-major rows x kpad, three BF16 slices + per-row scale exponent
+  int64_t rows = 0, kpad = 0;
+  uint16_t* s0 = nullptr;
+  uint16_t* s1 = nullptr;
+  uint16_t* s2 = nullptr;  // third slice, pre-scaled by 2^-8
+  uint16_t* s1h = nullptr; // second slice pre-scaled by 2^-8 (one operand only)
+  int* expo = nullptr;     // [rows]
+};
+// Slice an FP64 row-major matrix (rows x k, ld) into a SplitMatrix (zero padded to kpad).
+void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld, SplitMatrix& m, bool with_s1h,
+                       int nslices, cudaStream_t st);
+// C (FP64, rows of A x rows of B) = scale * A B^T through tcgen05 (see k_tcgen05.cu).
+// tiles: if symmetric_upper, only tiles with tile_row <= tile_col are computed and each tile is
+// also written transposed.  Returns false if the device path is unavailable.
+lrtei_status tc_gemm_split(const SplitMatrix& A, const SplitMatrix& B, int nslices, int64_t M, int64_t N,
+                           double scale, double* d_C, int64_t ldc, bool symmetric_upper, int* d_status,
+                           cudaStream_t st);
+
+}  // namespace lrtei

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (relative Frobenius norm unless stated):
+  FP64 path       1e-12   (both forms of Theorem 1)
+  FP32 CUDA-core  1e-5
+Sizes: the small s-only workload in full, scaled-down s/p/d contracted instances (several
+tiles and a ragged tail), and sampled rows of the full-size 180-function instance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_13069_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_fro(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2210_13069_gb300 import build_lib, lrtei
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build_lib.build()
+    lrtei.load()
+    return lrtei
+
+
+def mol_spd_small(seed=2001, natoms=2, nprim=3, n=12, P=12, omega=0.4):
+    return synth.random_molecule(seed, natoms=natoms, cube=4.0, nprim=nprim, alpha_range=(0.1, 50.0), omega=omega,
+                                 n=n, P=P)
+
+
+def mol_ragged(seed=2002):
+    """Shells with different contraction lengths (ragged I_mu I_nu) and l up to 2; N_b = 45."""
+    m = synth.random_molecule(seed, natoms=3, cube=5.0, nprim=2, alpha_range=(0.2, 30.0), omega=0.5, n=10, P=10)
+    rng = np.random.default_rng(seed)
+    for i, sh in enumerate(m.shells):
+        k = 1 + (i % 3)
+        sh.exps = np.sort(np.exp(rng.uniform(np.log(0.2), np.log(30.0), size=k)))[::-1].copy()
+        sh.coefs = rng.uniform(0.1, 1.0, size=k)
+    return m
+
+
+@pytest.mark.parametrize("form", ["hadamard", "factored"])
+def test_small_s_full_B_fp64(lib, form):
+    m = synth.workload_small_s()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "fp64")
+    B = pl.assemble_B(form).cpu().numpy()
+    pl.status()
+    assert rel_fro(B, ref) <= 1e-12
+    assert np.max(np.abs(B - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_factors_match_oracle(lib):
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    pl = lib.Plan(m, "fp64")
+    S, C, s, w, c = [t.cpu().numpy() for t in pl.factors()]
+    so, wo = o.nodes()
+    assert np.max(np.abs(s - so)) <= 1e-15 * m.omega
+    assert np.max(np.abs(w - wo) / wo) <= 1e-13
+    for d in range(3):
+        for p in range(m.P):
+            A = o.cheb(d, p)
+            assert np.max(np.abs(C[d, p] - A)) <= 1e-14 * np.abs(A).max()
+    # moments: rows ordered by unique pair (mu <= nu) then j = j1 * I_nu + j2
+    nbf = m.nbf
+    row = 0
+    for mu in range(nbf):
+        for nu in range(mu, nbf):
+            Wd = [o.moments(mu, nu, d) for d in range(3)]
+            I = Wd[0].shape[0]
+            for d in range(3):
+                got = S[d, row:row + I]
+                scale = np.abs(Wd[d]).max(axis=1, keepdims=True)
+                assert np.all(np.abs(got - Wd[d]) <= 1e-13 * scale + 1e-300), (mu, nu, d)
+            row += I
+    assert row == S.shape[1]
+
+
+@pytest.mark.parametrize("form", ["hadamard", "factored"])
+def test_contracted_spd_full_B_fp64(lib, form):
+    m = mol_spd_small()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "fp64")
+    B = pl.assemble_B(form).cpu().numpy()
+    assert rel_fro(B, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("form", ["hadamard", "factored"])
+def test_ragged_full_B_fp64(lib, form):
+    """N_b = 45 -> 1035 unique pairs: spans many 64-wide GEMM tiles with a ragged tail."""
+    m = mol_ragged()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "fp64")
+    B = pl.assemble_B(form).cpu().numpy()
+    assert rel_fro(B, ref) <= 1e-12
+    assert pl.info["npair"] == 1035
+
+
+def test_entries_algorithm1(lib):
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, m.nbf, size=(3000, 4)).astype(np.int32)
+    ref = o.entries(idx)
+    pl = lib.Plan(m, "fp64")
+    got = pl.entries(idx).cpu().numpy()
+    assert rel_fro(got, ref) <= 1e-12
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * scale
+
+
+def test_entries_empty_and_single_function(lib):
+    import torch
+    m = synth.random_molecule(9, natoms=1, cube=1.0, shells_per_atom=(("s", 1),), nprim=1, alpha_range=(0.5, 0.5),
+                              omega=0.3, n=6, P=4)
+    pl = lib.Plan(m, "fp64")
+    assert pl.nbf == 1
+    out = torch.empty(0, dtype=torch.float64, device="cuda")
+    idx = torch.empty((0, 4), dtype=torch.int32, device="cuda")
+    lib.lrtei_entries(pl.plan, idx, 0, out)
+    B = pl.assemble_B("hadamard").cpu().numpy()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    assert rel_fro(B, ref) <= 1e-13
+
+
+def test_explicit_box_and_n1_P1(lib):
+    """Degenerate orders n = 1, P = 1 and an explicit, non-cubic box."""
+    m = mol_spd_small(n=1, P=1)
+    m.box_lo = np.array([-3.0, -2.5, -4.0])
+    m.box_hi = np.array([7.0, 6.5, 5.0])
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "fp64")
+    for form in ("hadamard", "factored"):
+        B = pl.assemble_B(form).cpu().numpy()
+        assert rel_fro(B, ref) <= 1e-12
+
+
+def test_jbuild_fp64(lib):
+    import torch
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    D = synth.random_densities(11, m.nbf, 5)
+    ref = o.jbuild_factored(D)
+    pl = lib.Plan(m, "fp64")
+    J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+    assert rel_fro(J, ref) <= 1e-12
+    assert np.max(np.abs(J - J.transpose(0, 2, 1))) <= 1e-14 * np.abs(J).max()
+
+
+def test_fp32_path_error_stated(lib):
+    m = mol_spd_small()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "fp32")
+    B = pl.assemble_B("factored").cpu().numpy()
+    err = rel_fro(B, ref)
+    print(f"fp32 CUDA-core factored form: rel. Frobenius error {err:.3e}")
+    assert err <= 1e-5
+
+
+def test_full_size_180_sampled_rows(lib):
+    """The 180-function s/p/d instance at full size: sampled rows of B_u, both forms."""
+    m = synth.workload_spd()
+    o = oracle.Oracle.from_molecule(m)
+    pl = lib.Plan(m, "fp64")
+    nbf = m.nbf
+    rng = np.random.default_rng(17)
+    picks = [(0, 0), (int(rng.integers(0, nbf)), int(rng.integers(0, nbf))), (nbf - 1, nbf - 1)]
+    for mu, nu in picks:
+        mu, nu = min(mu, nu), max(mu, nu)
+        r = mu * nbf - mu * (mu - 1) // 2 + (nu - mu)
+        full = o.B_rows([mu * nbf + nu])[0]
+        # unique columns in pair order
+        cols = [ka * nbf + la for ka in range(nbf) for la in range(ka, nbf)]
+        ref = full[cols]
+        for form in ("hadamard", "factored"):
+            got = pl.Bu_rows(r, r + 1, form).cpu().numpy()[0]
+            assert rel_fro(got, ref) <= 1e-12, (mu, nu, form)
