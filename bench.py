@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="split_f16", choices=["split_f16", "fp64", "fp32", "bf16"])
     ap.add_argument("--form", default="factored", choices=["auto", "hadamard", "factored"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -268,9 +268,9 @@ def run_ours(args, world, rank, local):
     # ---- roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
     form_used = plan.info and lrtei.lrtei_plan_info_get(plan.plan)["last_form"]
-    if args.precision in ("split_bf16", "bf16"):
+    if args.precision in ("split_f16", "bf16"):
         kname, src = "tc_gemm", "paper_2210_13069_gb300/csrc/k_tcgen05.cu"
-        k_slices = 6 if args.precision == "split_bf16" else 1
+        k_slices = 6 if args.precision == "split_f16" else 1
         tot_ms, cnt = prof["tc_gemm"]
         # algorithmic flops per step of the tensor-core GEMMs: G = F K (npair x n3 x n3) and the
         # upper-triangular tiles of B_u = G F^T (npair^2 n3), one product each
@@ -359,7 +359,7 @@ def run_ours(args, world, rank, local):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        dtype = {"split_bf16": "bf16x3 (8-bit slices, fp32 acc)", "bf16": "bf16", "fp64": "f64", "fp32": "f32"}[
+        dtype = {"split_f16": "f16x3 (8+11+11-bit integer slices, fp32 acc)", "bf16": "bf16", "fp64": "f64", "fp32": "f32"}[
             args.precision]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -54,10 +54,12 @@ typedef enum {
 typedef enum {
   LRTEI_FP64 = 0,        /* FP64 CUDA-core contractions */
   LRTEI_FP32 = 1,        /* FP32 CUDA-core contractions */
-  LRTEI_SPLIT_BF16 = 2,  /* tcgen05 tensor cores, operands split into three 8-bit BF16 slices
-                            with per-row power-of-two scales, FP32 accumulation that is exact
-                            within each 256-deep K chunk, integer/FP32 accumulation across chunks */
-  LRTEI_BF16 = 3         /* tcgen05 tensor cores, one BF16 slice per operand (about 1e-3) */
+  LRTEI_SPLIT_F16 = 2,  /* tcgen05 tensor cores, split operands: per row a power-of-two scale and
+                            three integer slices (8 + 11 + 11 bits) held exactly in 16-bit floats;
+                            the leading products accumulate exactly in FP32 within each 256-deep K
+                            chunk, chunks are summed in int32 / FP32 registers (about 30 bits) */
+  LRTEI_BF16 = 3         /* tcgen05 tensor cores, plain BF16 operands (one rounding per element),
+                            FP32 accumulation */
 } lrtei_precision;
 
 /* Which of the two equivalent forms of Theorem 1 assembles B. */

@@ -1,0 +1,688 @@
+// k_tcgen05.cu -- tensor-core (tcgen05 + TMA + TMEM) GEMM of the factored form, sm_103a.
+//
+// C = scale * A B^T for FP64 matrices A (M x K) and B (N x K), both K-contiguous, through
+// integer slices held in FP16 (every slice is an integer or an integer times a power of two,
+// so the FP16 values are exact):
+//   x = 2^e (s0 2^-8 + t1 2^-19 + t2 2^-30),  e per row,  |s0| <= 255, |t1|, |t2| <= 1024.
+// Per 256-deep K chunk the tensor cores accumulate in TMEM (FP32):
+//   L0  = sum s0a s0b                      (products < 2^16, 256 of them: exact in FP32)
+//   L12 = sum s0a t1b + t1a s0b + s0a t2'b + t1a t1'b + t2'a s0b,   t' = t / 2^11
+// and the epilogue warps drain each chunk into registers: L0 into an int32 running sum
+// (exact for K <= 32768), L12 into an FP32 running sum.  The tile is written as
+//   C = scale 2^(ea+eb-16) (T0 + T12 / 2^11)  in FP64.
+// The leading term is exact whatever rounding the tensor core applies to its FP32 sums; the
+// rest carries 2^-11 of the weight.  The representation error is about 2^-31 of the row
+// maxima; the dropped products (t1 t2, t2 t1, t2 t2) are below 2^-29 of them.
+//
+// Kernel organisation (one 128 x BN output tile per CTA, 18 warps):
+//   warp 0       TMA producer: 3 A slices + 4 B slices per 64-deep K step into a ring of
+//                shared-memory stages (128-byte swizzle), mbarrier transaction counts
+//   warp 1       TMEM allocation (512 columns) and the single MMA-issuing thread:
+//                6 tcgen05.mma (M=128, N=BN, K=16) per 16-deep k step into two accumulators,
+//                double-buffered across K chunks
+//   warps 2..17  epilogue: tcgen05.ld of each finished chunk, running sums, staged FP64 store
+// Every mbarrier wait is bounded: on expiry the CTA raises the device status word, stops
+// issuing work, waits (bounded) for what it issued, frees TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "lrtei_internal.h"
+
+namespace lrtei {
+namespace tc {
+
+constexpr int BM = 128;      // rows of A per tile (MMA M)
+constexpr int BK = 64;       // K per pipeline stage (128-byte rows, 128B swizzle)
+constexpr int KCHUNK = 256;  // K per exact FP32 accumulation chunk
+constexpr int NA = 3;        // A slices: s0, t1, t2'
+constexpr int NB = 4;        // B slices: s0, t1, t1', t2'
+constexpr int kEpiWarps = 16;               // 4 per TMEM lane quadrant
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct Params {
+  int64_t M, N;
+  int64_t tiles_n;
+  int64_t ntiles;         // number of output tiles (upper triangle if symmetric)
+  int nchunks_total;      // kpad / KCHUNK
+  int chunks_per_split;
+  const int* ea;
+  const int* eb;
+  double scale;
+  double* C;
+  int64_t ldc;
+  int64_t split_stride;   // elements between split partials (splits > 1)
+  int transpose_out;
+  int symmetric;
+  int* status;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the CTA is aborting or the wait gave up (which raises the abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  long long t0 = clock64();
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        atomicExch(status, (int)kDevTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, void* dst, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with 128-byte swizzle: 8-row x 128-byte atoms, atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, D FP32, both K-major, M = 128, N = BN; A/B FP16 (format 0)
+// for the integer slices, BF16 (format 1) for plain BF16 operands.
+template <int BN, bool PLAIN>
+__device__ __forceinline__ uint32_t instr_desc() {
+  constexpr uint32_t f = PLAIN ? 1u : 0u;
+  return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ double pow2(int k) {  // 2^k, exponent clamped to the normal range
+  k = max(-1022, min(1023, k));
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// ------------------------------------------------------------------ the kernel
+// PLAIN: one BF16 operand plane each, one product per k step, FP32 sums (no exactness).
+template <int BN, int STAGES, bool PLAIN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
+              const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
+              const __grid_constant__ CUtensorMap tb1, const __grid_constant__ CUtensorMap tb1h,
+              const __grid_constant__ CUtensorMap tb2, const Params p) {
+  constexpr uint32_t A_BYTES = BM * BK * 2;
+  constexpr uint32_t B_BYTES = BN * BK * 2;
+  constexpr int NA_ = PLAIN ? 1 : NA, NB_ = PLAIN ? 1 : NB;
+  constexpr uint32_t STAGE_BYTES = NA_ * A_BYTES + NB_ * B_BYTES;
+  constexpr int KSTEPS = KCHUNK / BK;  // pipeline stages per chunk
+  constexpr int QC = BN / 4;           // columns per epilogue thread (4 warps per lane quadrant)
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 8 + (BM + BN) * 4;
+  constexpr uint32_t RING_BYTES = (STAGES * STAGE_BYTES > TILE_BYTES) ? STAGES * STAGE_BYTES : TILE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ((RING_BYTES + 7) & ~7u));
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;   // [2] accumulator buffer ready
+  uint64_t* acce = accf + 2;         // [2] accumulator buffer drained
+  uint64_t* done = acce + 2;         // all MMAs retired
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // tile coordinates
+  int64_t ti, tj;
+  const int64_t tile = blockIdx.x;
+  bool mirror_tile = false;
+  if (p.symmetric) {  // upper triangle of 128 x 128 blocks, each split into BM/BN column tiles
+    constexpr int SUB = BM / BN;
+    int64_t t = tile / SUB, r = 0, len = (p.tiles_n + SUB - 1) / SUB;
+    const int sub = (int)(tile % SUB);
+    while (t >= len) { t -= len; ++r; --len; }
+    ti = r;
+    tj = (r + t) * SUB + sub;
+    mirror_tile = (r + t) != r;  // strictly above the diagonal block: write the transpose too
+  } else {
+    ti = tile / p.tiles_n;
+    tj = tile % p.tiles_n;
+  }
+  const int64_t m0 = ti * BM, n0 = tj * BN;
+  const int split = blockIdx.y;
+  const int c_begin = split * p.chunks_per_split;
+  const int c_end = min(p.nchunks_total, c_begin + p.chunks_per_split);
+  const int nchunks = max(0, c_end - c_begin);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], kEpiWarps);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      const int nk = nchunks * KSTEPS;
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status)) break;
+        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+        uint8_t* st = smem + (size_t)s * STAGE_BYTES;
+        const int kx = (c_begin * KSTEPS + it) * BK;
+        uint8_t* sb = st + NA_ * A_BYTES;
+        tma_load_2d(&ta0, st + 0 * A_BYTES, &full[s], kx, (int)m0);
+        tma_load_2d(&tb0, sb + 0 * B_BYTES, &full[s], kx, (int)n0);
+        if constexpr (!PLAIN) {
+          tma_load_2d(&ta1, st + 1 * A_BYTES, &full[s], kx, (int)m0);
+          tma_load_2d(&ta2, st + 2 * A_BYTES, &full[s], kx, (int)m0);
+          tma_load_2d(&tb1, sb + 1 * B_BYTES, &full[s], kx, (int)n0);
+          tma_load_2d(&tb1h, sb + 2 * B_BYTES, &full[s], kx, (int)n0);
+          tma_load_2d(&tb2, sb + 3 * B_BYTES, &full[s], kx, (int)n0);
+        }
+        issued = it + 1;
+      }
+      // On abort, wait (bounded) for the loads still in flight before the CTA can exit.
+      if (*abort_flag) {
+        for (int it = max(0, issued - STAGES); it < issued; ++it) {
+          const int s = it % STAGES;
+          long long t0 = clock64();
+          while (!mbar_try_wait(&full[s], (uint32_t)(it / STAGES) & 1u) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc<BN, PLAIN>();
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int buf = c & 1;
+        if (!mbar_wait(&acce[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d0 = tmem_base + (uint32_t)(buf * 2 * BN);
+        const uint32_t d1 = d0 + BN;
+        for (int step = 0; step < KSTEPS; ++step) {
+          const int it = c * KSTEPS + step;
+          const int s = it % STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1u, abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
+          const uint64_t a0 = smem_desc(base), a1 = smem_desc(base + A_BYTES), a2 = smem_desc(base + 2 * A_BYTES);
+          const uint32_t bb = base + NA_ * A_BYTES;
+          const uint64_t b0 = smem_desc(bb), b1 = smem_desc(bb + B_BYTES), b1h = smem_desc(bb + 2 * B_BYTES),
+                         b2 = smem_desc(bb + 3 * B_BYTES);
+#pragma unroll 1
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t o = (uint64_t)((k * 32) >> 4);  // +32 bytes along K inside the swizzle atom
+            const uint32_t first = (step == 0 && k == 0) ? 0u : 1u;
+            mma_bf16(d0, a0 + o, b0 + o, idesc, first);
+            if constexpr (!PLAIN) {
+              mma_bf16(d1, a0 + o, b1 + o, idesc, first);
+              mma_bf16(d1, a1 + o, b0 + o, idesc, 1u);
+              mma_bf16(d1, a0 + o, b2 + o, idesc, 1u);
+              mma_bf16(d1, a1 + o, b1h + o, idesc, 1u);
+              mma_bf16(d1, a2 + o, b0 + o, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);  // stage s may be refilled once these MMAs retire
+        }
+        if (!ok) break;
+        mma_commit(&accf[buf]);
+      }
+      // retire every MMA this thread issued before TMEM is released
+      mma_commit(done);
+      long long t0 = clock64();
+      while (!mbar_try_wait(done, 0u) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue warps 2..17
+    const int ew = warp - 2;
+    const int quad = warp & 3;             // TMEM lane quadrant this warp may access
+    const int col0 = (ew >> 2) * QC;       // first column of this thread
+    const int row = quad * 32 + lane;      // row inside the tile
+    int T0[QC];
+    float T12[QC];
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      T0[j] = 0;
+      T12[j] = 0.f;
+    }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      // one lane waits, the warp reconverges before the .sync.aligned TMEM loads
+      int got = 1;
+      if (lane == 0) got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, abort_flag, p.status) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 2 * BN + col0);
+#pragma unroll
+      for (int j0 = 0; j0 < QC; j0 += 8) {
+        uint32_t r[8];
+        tmem_ld8(tbase + j0, r);
+        tmem_wait_ld();
+        if constexpr (PLAIN) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) T12[j0 + j] += __uint_as_float(r[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
+          tmem_ld8(tbase + BN + j0, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) T12[j0 + j] += __uint_as_float(r[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+    // Stage the finished tile through the (now idle) operand shared memory: every MMA has
+    // retired once the last accumulator buffer was signalled, and every TMA load was consumed.
+    constexpr int LDS = BN + 1;  // padded row stride (doubles) against bank conflicts
+    double* stile = reinterpret_cast<double*>(smem);
+    int* sea = reinterpret_cast<int*>(stile + BM * LDS);
+    int* seb = sea + BM;
+    const bool good = ok && !*abort_flag;
+    if (good) {
+#pragma unroll
+      for (int j = 0; j < QC; ++j)
+        stile[row * LDS + col0 + j] = PLAIN ? (double)T12[j] : (double)T0[j] + (double)T12[j] * (1.0 / 2048.0);
+    }
+    constexpr int NE = 32 * kEpiWarps;
+    const int et = threadIdx.x - 64;  // 0..NE-1 over the epilogue warps
+    if (et < BM) sea[et] = (m0 + et < p.M) ? p.ea[m0 + et] : 0;
+    if (et < BN) seb[et] = (n0 + et < p.N) ? p.eb[n0 + et] : 0;
+    asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
+    if (good && !*abort_flag) {
+      double* Cs = p.C + (int64_t)split * p.split_stride;
+      // On a diagonal block of a symmetric product only the upper triangle (gm <= gn) is
+      // kept and mirrored, so that C comes out exactly symmetric.
+      const bool diag = p.symmetric && !mirror_tile;
+      if (!p.transpose_out) {  // row-major: consecutive threads along a row
+        for (int idx = et; idx < BM * BN; idx += NE) {
+          const int r = idx / BN, c = idx % BN;
+          const int64_t gm = m0 + r, gn = n0 + c;
+          if (gm < p.M && gn < p.N && (!diag || gm <= gn))
+            Cs[gm * p.ldc + gn] = p.scale * pow2(sea[r] + seb[c] - 16) * stile[r * LDS + c];
+        }
+      }
+      if (p.transpose_out || p.symmetric) {  // C^T: consecutive threads along a column of C
+        for (int idx = et; idx < BM * BN; idx += NE) {
+          const int c = idx / BM, r = idx % BM;
+          const int64_t gm = m0 + r, gn = n0 + c;
+          if (gm < p.M && gn < p.N && (!diag || gm < gn))
+            Cs[gn * p.ldc + gm] = p.scale * pow2(sea[r] + seb[c] - 16) * stile[r * LDS + c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ slicing
+__device__ __forceinline__ uint16_t f16_bits(float f) {
+  __half h = __float2half_rn(f);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+
+// One block per row: e with max|x| * 256/255 < 2^e, v = x 2^(8-e) in (-255, 255), then
+// s0 = rint(v), t1 = rint((v - s0) 2^11), t2 = rint(((v - s0) 2^11 - t1) 2^11).
+// Stored as FP16: s0, t1, t2 / 2^11 and (optionally) t1 / 2^11 -- all exact.
+__global__ void k_split_rows(const double* __restrict__ src, int64_t rows, int64_t k, int64_t ld, int64_t kpad,
+                             uint16_t* __restrict__ s0, uint16_t* __restrict__ s1, uint16_t* __restrict__ s2,
+                             uint16_t* __restrict__ s1h, int* __restrict__ expo, int nslices) {
+  __shared__ double red[32];
+  const int64_t r = blockIdx.x;
+  const double* x = src + r * ld;
+  double mx = 0.0;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) mx = fmax(mx, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  mx = red[0];
+  int e = 0;
+  if (mx > 0.0) frexp(mx * (256.0 / 255.0), &e);
+  if (e < -1000) mx = 0.0;  // treat rows below ~1e-301 as zero
+  if (threadIdx.x == 0) expo[r] = e;
+  const double sc = pow2(8 - e);
+  for (int64_t i = threadIdx.x; i < kpad; i += blockDim.x) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    if (i < k && mx > 0.0) {
+      const double v = x[i] * sc;  // |v| < 255
+      const double q0 = rint(v);
+      const double r1 = (v - q0) * 2048.0;
+      const double q1 = rint(r1);
+      const double q2 = rint((r1 - q1) * 2048.0);
+      a = (float)q0;
+      b = nslices > 1 ? (float)q1 : 0.f;
+      c = nslices > 2 ? (float)q2 : 0.f;
+    }
+    const int64_t o = r * kpad + i;
+    s0[o] = f16_bits(a);
+    s1[o] = f16_bits(b);
+    s2[o] = f16_bits(c * (1.0f / 2048.0f));
+    if (s1h) s1h[o] = f16_bits(b * (1.0f / 2048.0f));
+  }
+}
+
+// Plain BF16 operands: one rounded copy per element, exponent 8 so that the epilogue scale
+// 2^(ea + eb - 16) is 1.
+__global__ void k_plain_rows(const double* __restrict__ src, int64_t rows, int64_t k, int64_t ld, int64_t kpad,
+                             uint16_t* __restrict__ s0, int* __restrict__ expo) {
+  const int64_t r = blockIdx.x;
+  if (threadIdx.x == 0) expo[r] = 8;
+  for (int64_t i = threadIdx.x; i < kpad; i += blockDim.x) {
+    const float v = i < k ? (float)src[r * ld + i] : 0.f;
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    s0[r * kpad + i] = *reinterpret_cast<uint16_t*>(&h);
+  }
+}
+
+// 32 x 32 tiled transpose of an FP64 matrix: out (cols x rows) = in (rows x cols)^T.
+__global__ void k_transpose(const double* __restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
+                            double* __restrict__ out, int64_t ldo) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[r * ldi + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * ldo + r] = t[threadIdx.x][i];
+  }
+}
+
+// Sum of split-K partials: out[i] = sum_s part[s * stride + i] (row-major rows x cols, ld).
+__global__ void k_reduce_splits(const double* __restrict__ part, int splits, int64_t stride, int64_t rows,
+                                int64_t cols, int64_t ld, double* __restrict__ out, int64_t ldo) {
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / cols, j = t % cols;
+    double s = 0.0;
+    for (int q = 0; q < splits; ++q) s += part[q * stride + i * ld + j];
+    out[i * ldo + j] = s;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+static bool encode_plane(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t kpad, int box_rows, bool bf16) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(kpad * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES, bool PLAIN>
+static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits,
+                              cudaStream_t st) {
+  CUtensorMap m[7];
+  bool ok;
+  if (PLAIN) {
+    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, true) && encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, true);
+    m[1] = m[2] = m[0];
+    m[4] = m[5] = m[6] = m[3];
+  } else {
+    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, false) && encode_plane(&m[1], A.s1, A.rows, A.kpad, BM, false) &&
+         encode_plane(&m[2], A.s2, A.rows, A.kpad, BM, false) && encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, false) &&
+         encode_plane(&m[4], B.s1, B.rows, B.kpad, BN, false) && encode_plane(&m[5], B.s1h, B.rows, B.kpad, BN, false) &&
+         encode_plane(&m[6], B.s2, B.rows, B.kpad, BN, false);
+  }
+  if (!ok) {
+    set_error("cuTensorMapEncodeTiled failed (driver entry point unavailable or bad operand layout)");
+    return LRTEI_ERR_CUDA;
+  }
+  constexpr size_t stage = (size_t)(PLAIN ? 1 : NA) * BM * BK * 2 + (size_t)(PLAIN ? 1 : NB) * BN * BK * 2;
+  const size_t tile_bytes = (size_t)BM * (BN + 1) * 8 + (BM + BN) * 4;
+  const size_t smem = std::max(STAGES * stage, tile_bytes) + 1024 + 256;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gemm<BN, STAGES, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "tc_gemm smem attribute");
+  dim3 grid((unsigned)p.ntiles, (unsigned)splits);
+  count_launch();
+  k_tc_gemm<BN, STAGES, PLAIN><<<grid, kThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tc_gemm launch");
+  return LRTEI_OK;
+}
+
+}  // namespace tc
+
+void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld, SplitMatrix& m, bool with_s1h,
+                       int nslices, cudaStream_t st) {
+  if (rows <= 0) return;
+  count_launch();
+  if (m.plain) {
+    tc::k_plain_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.expo);
+    return;
+  }
+  tc::k_split_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2,
+                                                   with_s1h ? m.s1h : nullptr, m.expo, nslices);
+}
+
+void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,
+                      cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
+  count_launch();
+  tc::k_transpose<<<grid, block, 0, st>>>(in, rows, cols, ldi, out, ldo);
+}
+
+void launch_reduce_splits(const double* part, int splits, int64_t stride, int64_t rows, int64_t cols, int64_t ld,
+                          double* out, int64_t ldo, cudaStream_t st) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return;
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  count_launch();
+  tc::k_reduce_splits<<<(unsigned)b, 256, 0, st>>>(part, splits, stride, rows, cols, ld, out, ldo);
+}
+
+// C = scale * A B^T.  A: M rows (slices s0,s1,s2), B: N rows (slices s0,s1,s1h,s2), same kpad
+// (multiple of 256, <= 32768 per split).  d_C: FP64, ldc; transpose_out writes C^T.
+// When splits > 1, d_part (splits * M * N doubles) receives the partials, which are reduced into d_C.
+lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int64_t N, double scale, double* d_C,
+                     int64_t ldc, bool transpose_out, bool symmetric_upper, int splits, double* d_part,
+                     int* d_status, cudaStream_t st) {
+  if (A.kpad != B.kpad || A.kpad % tc::KCHUNK != 0) {
+    set_error("tc_gemm: operands must share a K padded to a multiple of %d", tc::KCHUNK);
+    return LRTEI_ERR_ARG;
+  }
+  const int nchunks = (int)(A.kpad / tc::KCHUNK);
+  splits = std::max(1, std::min(splits, nchunks));
+  int cps = (nchunks + splits - 1) / splits;
+  if ((int64_t)cps * tc::KCHUNK > 32768) {
+    set_error("tc_gemm: more than 32768 K per split (use more splits)");
+    return LRTEI_ERR_UNSUPPORTED;
+  }
+  splits = (nchunks + cps - 1) / cps;
+  if (symmetric_upper && (splits != 1 || M != N || transpose_out)) {
+    set_error("tc_gemm: symmetric mode needs one split and a square output");
+    return LRTEI_ERR_ARG;
+  }
+  tc::Params p{};
+  p.M = M;
+  p.N = N;
+  p.nchunks_total = nchunks;
+  p.chunks_per_split = cps;
+  p.ea = A.expo;
+  p.eb = B.expo;
+  p.scale = scale;
+  p.transpose_out = transpose_out ? 1 : 0;
+  p.symmetric = symmetric_upper ? 1 : 0;
+  p.status = d_status;
+  // 128 x 64 tiles: a 128 x 128 tile's running sums (two words per element) exceed the
+  // register file share of the epilogue warps.
+  const int BN = (N <= 32) ? 32 : 64;
+  const int64_t tiles_m = (M + tc::BM - 1) / tc::BM, tiles_n = (N + BN - 1) / BN;
+  p.tiles_n = tiles_n;
+  if (symmetric_upper) {
+    // upper-triangular enumeration in units of 128 x 128 blocks, each done as two 128 x 64 tiles
+    p.ntiles = tiles_m * (tiles_m + 1) / 2 * (tc::BM / BN);
+  } else {
+    p.ntiles = tiles_m * tiles_n;
+  }
+  if (splits > 1) {
+    if (!d_part) {
+      set_error("tc_gemm: split-K needs a partial buffer");
+      return LRTEI_ERR_ARG;
+    }
+    p.C = d_part;
+    p.ldc = transpose_out ? M : N;
+    p.split_stride = M * N;
+  } else {
+    p.C = d_C;
+    p.ldc = ldc;
+    p.split_stride = 0;
+  }
+  lrtei_status s;
+  {
+    ProfScope ps("tc_gemm", st);
+    const bool plain = A.plain;
+    if (plain != B.plain) {
+      set_error("tc_gemm: operands must both be plain or both split");
+      return LRTEI_ERR_ARG;
+    }
+    if (BN == 64)
+      s = plain ? tc::launch_tc<64, 4, true>(A, B, p, splits, st) : tc::launch_tc<64, 2, false>(A, B, p, splits, st);
+    else
+      s = plain ? tc::launch_tc<32, 4, true>(A, B, p, splits, st) : tc::launch_tc<32, 3, false>(A, B, p, splits, st);
+  }
+  if (s != LRTEI_OK) return s;
+  if (splits > 1) {
+    if (transpose_out)
+      launch_reduce_splits(d_part, splits, M * N, N, M, M, d_C, ldc, st);
+    else
+      launch_reduce_splits(d_part, splits, M * N, M, N, N, d_C, ldc, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "reduce_splits");
+  }
+  return LRTEI_OK;
+}
+
+}  // namespace lrtei

@@ -68,6 +68,8 @@ struct lrtei_plan {
   double* d_T = nullptr;      // Hadamard: 3 * P * nrows * n
   double* d_F = nullptr;      // factored: npair * n^3 (FP64)
   float* d_F32 = nullptr;     // factored: npair * n^3 (FP32)
+  SplitMatrix Fsp, Ksp, FTsp; // tensor-core operands: F_u, K, F_u^T as BF16 slices
+  bool have_Fsp = false, have_Ksp = false, have_FTsp = false;
   std::vector<void*> allocs;
   size_t bytes = 0;
 
@@ -404,6 +406,37 @@ lrtei_status ensure_F32(lrtei_plan* pl, cudaStream_t st) {
   return finish_launch("build_F32");
 }
 
+bool is_split(const lrtei_plan* pl) { return pl->prec == LRTEI_SPLIT_F16 || pl->prec == LRTEI_BF16; }
+int nslices(const lrtei_plan* pl) { return pl->prec == LRTEI_BF16 ? 1 : 3; }
+
+lrtei_status alloc_split(lrtei_plan* pl, SplitMatrix& m, int64_t rows, int64_t k, bool with_s1h) {
+  m.rows = rows;
+  m.kpad = kpad256(k);
+  m.plain = pl->prec == LRTEI_BF16;
+  const size_t cnt = (size_t)rows * m.kpad;
+  LRTEI_TRY(pl->alloc(&m.s0, cnt));
+  if (!m.plain) {
+    LRTEI_TRY(pl->alloc(&m.s1, cnt));
+    LRTEI_TRY(pl->alloc(&m.s2, cnt));
+    if (with_s1h) LRTEI_TRY(pl->alloc(&m.s1h, cnt));
+  }
+  LRTEI_TRY(pl->alloc(&m.expo, rows));
+  return LRTEI_OK;
+}
+
+lrtei_status ensure_Fsp(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->have_Fsp) return LRTEI_OK;
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
+  LRTEI_TRY(ensure_F64(pl, st));
+  LRTEI_TRY(alloc_split(pl, pl->Fsp, pl->t.npair, n3, true));
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(pl->d_F, pl->t.npair, n3, n3, pl->Fsp, true, nslices(pl), st);
+  }
+  pl->have_Fsp = true;
+  return finish_launch("split F");
+}
+
 // Scratch buffer owned by the call (freed at the end of the call, stream-ordered).
 struct Scratch {
   std::vector<void*> ptrs;
@@ -427,7 +460,91 @@ struct Scratch {
   }
 };
 
+lrtei_status ensure_Ksp(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->have_Ksp) return LRTEI_OK;
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
+  Scratch sc(st);
+  double* K;
+  LRTEI_TRY(sc.get(&K, (size_t)n3 * n3));
+  launch_build_K(pl->n, pl->P, pl->d_C, pl->d_w, K, st);
+  LRTEI_TRY(alloc_split(pl, pl->Ksp, n3, n3, true));
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(K, n3, n3, n3, pl->Ksp, true, nslices(pl), st);
+  }
+  pl->have_Ksp = true;
+  return finish_launch("split K");
+}
+
+lrtei_status ensure_FTsp(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->have_FTsp) return LRTEI_OK;
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n, npair = pl->t.npair;
+  LRTEI_TRY(ensure_F64(pl, st));
+  Scratch sc(st);
+  double* FT;
+  LRTEI_TRY(sc.get(&FT, (size_t)n3 * npair));
+  launch_transpose(pl->d_F, npair, n3, n3, FT, npair, st);
+  LRTEI_TRY(alloc_split(pl, pl->FTsp, n3, npair, false));
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(FT, n3, npair, npair, pl->FTsp, false, nslices(pl), st);
+  }
+  pl->have_FTsp = true;
+  return finish_launch("split F^T");
+}
+
+// A scratch split operand (planes owned by the call).
+lrtei_status scratch_split(Scratch& sc, SplitMatrix& m, int64_t rows, int64_t k, bool with_s1h, bool plain) {
+  m.rows = rows;
+  m.kpad = kpad256(k);
+  m.plain = plain;
+  const size_t cnt = (size_t)rows * m.kpad;
+  LRTEI_TRY(sc.get(&m.s0, cnt));
+  if (!plain) {
+    LRTEI_TRY(sc.get(&m.s1, cnt));
+    LRTEI_TRY(sc.get(&m.s2, cnt));
+    if (with_s1h) LRTEI_TRY(sc.get(&m.s1h, cnt));
+  }
+  LRTEI_TRY(sc.get(&m.expo, rows));
+  return LRTEI_OK;
+}
+
+int splits_for(int64_t M, int64_t K) {
+  const int64_t tiles = (M + 127) / 128;
+  int64_t s = (kpad256(K) + 32767) / 32768;
+  while (tiles * s < 2 * 152 && s * 256 * 2 <= kpad256(K)) s *= 2;
+  return (int)s;
+}
+
+// Rows [r0, r1) of B_u through the tensor-core GEMMs (split precision), prefactor included.
+lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int64_t ld, cudaStream_t st) {
+  const double pref = pl->omega / sqrt(3.14159265358979323846);
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n, npair = pl->t.npair, nr = r1 - r0;
+  LRTEI_TRY(ensure_Fsp(pl, st));
+  LRTEI_TRY(ensure_Ksp(pl, st));
+  Scratch sc(st);
+  double* G;
+  LRTEI_TRY(sc.get(&G, (size_t)nr * n3));
+  SplitMatrix Fr = pl->Fsp;  // row view [r0, r1)
+  Fr.rows = nr;
+  Fr.s0 += r0 * Fr.kpad;
+  if (Fr.s1h) Fr.s1h += r0 * Fr.kpad;
+  if (Fr.s1) Fr.s1 += r0 * Fr.kpad;
+  if (Fr.s2) Fr.s2 += r0 * Fr.kpad;
+  Fr.expo += r0;
+  LRTEI_TRY(tc_gemm(Fr, pl->Ksp, nr, n3, 1.0, G, n3, false, false, 1, nullptr, pl->d_status, st));
+  SplitMatrix Gs;
+  LRTEI_TRY(scratch_split(sc, Gs, nr, n3, false, pl->prec == LRTEI_BF16));
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(G, nr, n3, n3, Gs, false, nslices(pl), st);
+  }
+  const bool sym = (r0 == 0 && r1 == npair && ld == npair);
+  return tc_gemm(Gs, pl->Fsp, nr, npair, pref, out, ld, false, sym, 1, nullptr, pl->d_status, st);
+}
+
 int choose_form(const lrtei_plan* pl, lrtei_form form) {
+  if (is_split(pl)) return LRTEI_FORM_FACTORED;  // the tensor-core path runs the factored form
   if (form == LRTEI_FORM_HADAMARD || form == LRTEI_FORM_FACTORED) return form;
   // Hadamard: ~ npair^2 * P * Ibar^2 * (6n + 3); factored: ~ npair^2 n^3 + 6 P n^4 npair.
   const double Ibar2 = (double)pl->t.nrows / pl->t.npair;
@@ -442,6 +559,7 @@ lrtei_status bu_rows(lrtei_plan* pl, int form, int64_t r0, int64_t r1, double* o
   const int n = pl->n, P = pl->P;
   const int64_t npair = pl->t.npair, n3 = (int64_t)n * n * n, nr = r1 - r0;
   if (nr <= 0) return LRTEI_OK;
+  if (is_split(pl)) return bu_rows_tc(pl, r0, r1, out, ld, st);
   if (form == LRTEI_FORM_HADAMARD) {
     LRTEI_TRY(ensure_T(pl, st));
     {
@@ -517,6 +635,7 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
     rb = std::max<int64_t>(1, std::min<int64_t>(rb, (int64_t)((1ULL << 30) / (sizeof(double) * 3 * (size_t)n3))));
   }
   rb = std::min(rb, npair);
+  if (is_split(plan)) rb = npair;  // one symmetric tensor-core pass over the whole B_u
   Scratch sc(st);
   double* blk;
   LRTEI_TRY(sc.get(&blk, (size_t)rb * npair));
@@ -565,10 +684,57 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
   return LRTEI_OK;
 }
 
+static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st) {
+  const int nbf = plan->basis.nbf, n = plan->n;
+  const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;
+  const double pref = plan->omega / sqrt(kPi);
+  LRTEI_TRY(ensure_Fsp(plan, st));
+  LRTEI_TRY(ensure_Ksp(plan, st));
+  LRTEI_TRY(ensure_FTsp(plan, st));
+  Scratch sc(st);
+  double *Du, *DuT, *XT, *YT, *Ju, *part;
+  LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&DuT, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&XT, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&YT, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Ju, (size_t)npair * R));
+  const int s1 = splits_for(n3, npair), s2 = splits_for(n3, n3), s3 = splits_for(npair, n3);
+  const int smax = std::max(s1, std::max(s2, s3));
+  LRTEI_TRY(sc.get(&part, (size_t)smax * std::max(n3, npair) * R));
+  SplitMatrix Dsp, Xsp, Ysp;
+  LRTEI_TRY(scratch_split(sc, Dsp, R, npair, true, plan->prec == LRTEI_BF16));
+  LRTEI_TRY(scratch_split(sc, Xsp, R, n3, true, plan->prec == LRTEI_BF16));
+  LRTEI_TRY(scratch_split(sc, Ysp, R, n3, true, plan->prec == LRTEI_BF16));
+  launch_pack_density(nbf, R, d_D, Du, st);
+  launch_transpose(Du, npair, R, R, DuT, npair, st);
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(DuT, R, npair, npair, Dsp, true, nslices(plan), st);
+  }
+  // X^T = (F^T D_u)^T : R x n^3
+  LRTEI_TRY(tc_gemm(plan->FTsp, Dsp, n3, R, 1.0, XT, n3, true, false, s1, part, plan->d_status, st));
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(XT, R, n3, n3, Xsp, true, nslices(plan), st);
+  }
+  // Y^T = (K X)^T : R x n^3  (K symmetric)
+  LRTEI_TRY(tc_gemm(plan->Ksp, Xsp, n3, R, 1.0, YT, n3, true, false, s2, part, plan->d_status, st));
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(YT, R, n3, n3, Ysp, true, nslices(plan), st);
+  }
+  // J_u = F Y : npair x R
+  LRTEI_TRY(tc_gemm(plan->Fsp, Ysp, npair, R, 1.0, Ju, R, false, false, s3, part, plan->d_status, st));
+  launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+  return finish_launch("jbuild (tensor cores)");
+}
+
 lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream) {
   if (!plan || !d_D || !d_J) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
   if (R <= 0) { set_error("R must be positive (got %d)", R); return LRTEI_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
+  ProfScope ps_all("jbuild", st);
+  if (is_split(plan)) return jbuild_tc(plan, d_D, R, d_J, st);
   const int nbf = plan->basis.nbf, n = plan->n, P = plan->P;
   const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;
   const double pref = plan->omega / sqrt(kPi);
@@ -583,9 +749,18 @@ lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_
   launch_pack_density(nbf, R, d_D, Du, st);
   LRTEI_TRY(ensure_F64(plan, st));
   // Xt = Du^T F  (R x n^3); Yt = kron(Xt); Ju = F Yt^T (npair x R)
-  gemm_cuda_core<double>(true, false, R, n3, npair, 1.0, Du, R, plan->d_F, n3, 0.0, Xt, n3, st);
-  launch_kron_apply(n, P, plan->d_C, plan->d_w, Xt, Yt, R, t1, t2, st);
-  gemm_cuda_core<double>(false, true, npair, R, n3, 1.0, plan->d_F, n3, Yt, n3, 0.0, Ju, R, st);
+  {
+    ProfScope ps("gemm_fp64", st);
+    gemm_cuda_core<double>(true, false, R, n3, npair, 1.0, Du, R, plan->d_F, n3, 0.0, Xt, n3, st);
+  }
+  {
+    ProfScope ps("kron", st);
+    launch_kron_apply(n, P, plan->d_C, plan->d_w, Xt, Yt, R, t1, t2, st);
+  }
+  {
+    ProfScope ps("gemm_fp64", st);
+    gemm_cuda_core<double>(false, true, npair, R, n3, 1.0, plan->d_F, n3, Yt, n3, 0.0, Ju, R, st);
+  }
   launch_unpack_J(nbf, R, Ju, pref, d_J, st);
   return finish_launch("jbuild");
 }

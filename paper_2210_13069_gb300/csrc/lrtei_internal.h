@@ -121,22 +121,29 @@ void convert_f64_to_f32(const double* in, float* out, int64_t count, cudaStream_
 void convert_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t st);
 
 // ---------------------------------------------------------------- tensor cores (tcgen05)
-struct SplitMatrix {  // row-major rows x kpad, three BF16 slices + per-row scale exponent
+struct SplitMatrix {  // row-major rows x kpad, three FP16 integer slices + per-row scale exponent
   int64_t rows = 0, kpad = 0;
   uint16_t* s0 = nullptr;
   uint16_t* s1 = nullptr;
-  uint16_t* s2 = nullptr;  // third slice, pre-scaled by 2^-8
-  uint16_t* s1h = nullptr; // second slice pre-scaled by 2^-8 (one operand only)
+  uint16_t* s2 = nullptr;  // third slice t2, pre-scaled by 2^-11 (FP16 bits)
+  uint16_t* s1h = nullptr; // second slice t1 pre-scaled by 2^-11 (B operand only)
   int* expo = nullptr;     // [rows]
+  bool plain = false;      // plain BF16 operands in s0 only (no slices)
 };
 // Slice an FP64 row-major matrix (rows x k, ld) into a SplitMatrix (zero padded to kpad).
 void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld, SplitMatrix& m, bool with_s1h,
                        int nslices, cudaStream_t st);
-// C (FP64, rows of A x rows of B) = scale * A B^T through tcgen05 (see k_tcgen05.cu).
-// tiles: if symmetric_upper, only tiles with tile_row <= tile_col are computed and each tile is
-// also written transposed.  Returns false if the device path is unavailable.
-lrtei_status tc_gemm_split(const SplitMatrix& A, const SplitMatrix& B, int nslices, int64_t M, int64_t N,
-                           double scale, double* d_C, int64_t ldc, bool symmetric_upper, int* d_status,
-                           cudaStream_t st);
+// nslices == 1 keeps only the leading slice (s1 = s2 = 0): plain BF16 operands.
+// C = scale * A B^T through tcgen05 (see k_tcgen05.cu).  A: M rows with slices s0, s1, s2;
+// B: N rows with s0, s1, s1h, s2; shared kpad (multiple of 256).  transpose_out writes C^T;
+// symmetric_upper computes the upper-triangular 128x128 blocks of a square C and mirrors them.
+// splits > 1 splits K (at most 32768 per split) into d_part (splits * M * N doubles), reduced
+// into C afterwards.
+lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int64_t N, double scale, double* d_C,
+                     int64_t ldc, bool transpose_out, bool symmetric_upper, int splits, double* d_part,
+                     int* d_status, cudaStream_t st);
+void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,
+                      cudaStream_t st);
+inline int64_t kpad256(int64_t k) { return (k + 255) / 256 * 256; }
 
 }  // namespace lrtei

@@ -186,3 +186,86 @@ def test_full_size_180_sampled_rows(lib):
         for form in ("hadamard", "factored"):
             got = pl.Bu_rows(r, r + 1, form).cpu().numpy()[0]
             assert rel_fro(got, ref) <= 1e-12, (mu, nu, form)
+
+
+# ------------------------------------------------------------------ tensor-core (split BF16) path
+
+@pytest.mark.parametrize("maker", ["small_s", "spd_small", "ragged"])
+def test_split_f16_full_B(lib, maker):
+    """tcgen05 path (8+11+11-bit integer slices, exact leading products): rel. Frobenius <= 1e-7."""
+    m = {"small_s": synth.workload_small_s, "spd_small": mol_spd_small, "ragged": mol_ragged}[maker]()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "split_f16")
+    B = pl.assemble_B("auto").cpu().numpy()
+    pl.status()
+    err = rel_fro(B, ref)
+    print(f"split_f16 {maker}: N_b={m.nbf} rel. Frobenius error {err:.3e}")
+    assert err <= 1e-7
+    # the factored form on the tensor cores is exactly symmetric (mirrored tiles)
+    assert np.array_equal(B, B.T)
+
+
+@pytest.mark.parametrize("maker", ["spd_small", "ragged"])
+def test_plain_bf16_error_stated(lib, maker):
+    """Plain BF16 operands with FP32 accumulation: rel. Frobenius <= 1e-3."""
+    m = {"spd_small": mol_spd_small, "ragged": mol_ragged}[maker]()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "bf16")
+    B = pl.assemble_B().cpu().numpy()
+    err = rel_fro(B, ref)
+    print(f"plain bf16 {maker}: rel. Frobenius error {err:.3e}")
+    assert err <= 1e-3
+
+
+def test_split_f16_jbuild(lib):
+    import torch
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    D = synth.random_densities(12, m.nbf, 7)
+    ref = o.jbuild_factored(D)
+    pl = lib.Plan(m, "split_f16")
+    J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+    pl.status()
+    err = rel_fro(J, ref)
+    print(f"split_f16 J-build: rel. Frobenius error {err:.3e}")
+    assert err <= 1e-7
+
+
+def test_split_f16_full_size_180(lib):
+    """Full-size 180-function instance: sampled rows of B (tensor-core row path and the full
+    symmetric assembly) against the oracle, the whole B against the FP64 GPU path (within 1e-12
+    of the oracle on sampled rows above), and a 32-density J-build against the FP64 GPU path."""
+    import torch
+    m = synth.workload_spd()
+    o = oracle.Oracle.from_molecule(m)
+    nbf = m.nbf
+    pl = lib.Plan(m, "split_f16")
+    full = pl.assemble_B()
+    rng = np.random.default_rng(23)
+    picks = [(0, 0), (int(rng.integers(0, nbf)), int(rng.integers(0, nbf))), (nbf - 1, nbf - 1), (3, 170)]
+    cols = [ka * nbf + la for ka in range(nbf) for la in range(ka, nbf)]
+    refs, rows_tc, rows_full = [], [], []
+    for mu, nu in picks:
+        mu, nu = min(mu, nu), max(mu, nu)
+        r = mu * nbf - mu * (mu - 1) // 2 + (nu - mu)
+        ref_full = o.B_rows([mu * nbf + nu])[0]
+        refs.append(ref_full)
+        rows_tc.append(pl.Bu_rows(r, r + 1).cpu().numpy()[0])
+        rows_full.append(full[mu * nbf + nu].cpu().numpy())
+    refs = np.array(refs)
+    e_rows = rel_fro(np.array(rows_tc), refs[:, cols])
+    e_full_rows = rel_fro(np.array(rows_full), refs)
+    print(f"split_f16 180 functions, sampled rows: rel. Frobenius {e_rows:.3e} (row path), {e_full_rows:.3e} (assembly)")
+    assert e_rows <= 1e-7 and e_full_rows <= 1e-7
+    p64 = lib.Plan(m, "fp64")
+    B64 = p64.assemble_B()
+    e_all = float(torch.linalg.norm(full - B64) / torch.linalg.norm(B64))
+    print(f"split_f16 180 functions, whole B vs FP64 GPU path: rel. Frobenius {e_all:.3e}")
+    assert e_all <= 1e-7
+    del full, B64
+    D = torch.as_tensor(synth.random_densities(31, nbf, 32), device="cuda")
+    J = pl.jbuild(D)
+    J64 = p64.jbuild(D)
+    err = float(torch.linalg.norm(J - J64) / torch.linalg.norm(J64))
+    print(f"split_f16 J-build, 180 functions, 32 densities: rel. error vs FP64 {err:.3e}")
+    assert err <= 1e-7
