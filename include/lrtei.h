@@ -120,6 +120,19 @@ lrtei_status lrtei_assemble_Bu_rows(lrtei_plan* plan, lrtei_form form, int64_t r
  * d_idx4: device int32[4*count] of (mu, nu, ka, la); d_out: device double[count]. */
 lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out, void* stream);
 
+/* ---- entries without device allocation ---------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate device
+ * memory where they need integrals (memory held by their own pool, paths where the device-wide
+ * synchronisation of cudaMalloc/cudaFree is not acceptable).  Same arguments and results as
+ * lrtei_entries, computed from the plan's resident moments and Chebyshev coefficients; it calls
+ * no allocator.  Its scratch is one fixed device array per device, 4 MiB, held while the
+ * library is loaded: at most 262144 entries per call (more returns LRTEI_ERR_UNSUPPORTED).  All
+ * calls on a device share the array, so calls whose kernels overlap on the GPU race.  The
+ * first call on a device performs a one-time lookup of the array's address with that device
+ * current; make that first call before any stream capture begins. */
+lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out,
+                                   void* stream);
+
 /* ---- factors (Theorem 1: w_p, s_p, A^(p), W~ = S_d) ---------------------------------------
  * Any pointer may be NULL.  d_s, d_w: P doubles; d_C: 3*P*n*n (d, p, a, b); d_S: 3*nrows*n
  * (d, row, m), rows ordered by unique pair then j = j1*I_nu + j2; d_c: nrows coefficients c_j. */

@@ -773,3 +773,21 @@ lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const doub
 }
 
 }  // extern "C"
+
+namespace lrtei {
+lrtei_status plan_view(const lrtei_plan* plan, PlanView* v) {
+  if (!plan || !v) {
+    set_error("NULL argument");
+    return LRTEI_ERR_ARG;
+  }
+  v->nbf = plan->basis.nbf;
+  v->n = plan->n;
+  v->P = plan->P;
+  v->omega = plan->omega;
+  v->t = &plan->t;
+  v->S = plan->d_S;
+  v->C = plan->d_C;
+  v->w = plan->d_w;
+  return LRTEI_OK;
+}
+}  // namespace lrtei

@@ -146,4 +146,16 @@ void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi,
                       cudaStream_t st);
 inline int64_t kpad256(int64_t k) { return (k + 255) / 256 * 256; }
 
+// Read-only view of a plan's resident device tables (for entry points defined outside
+// lrtei_api.cu).
+struct PlanView {
+  int nbf, n, P;
+  double omega;
+  const PairTable* t;
+  const double* S;  // 3 x nrows x n moments
+  const double* C;  // 3 x P x n x n Chebyshev coefficients
+  const double* w;  // P quadrature weights
+};
+lrtei_status plan_view(const lrtei_plan* plan, PlanView* v);
+
 }  // namespace lrtei

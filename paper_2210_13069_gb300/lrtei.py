@@ -70,6 +70,7 @@ def load():
         "lrtei_assemble_B": (S, [VP, ctypes.c_int, VP, ctypes.c_int64, VP]),
         "lrtei_assemble_Bu_rows": (S, [VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, VP, ctypes.c_int64, VP]),
         "lrtei_entries": (S, [VP, VP, ctypes.c_int64, VP, VP]),
+        "lrtei_entries_noalloc": (S, [VP, VP, ctypes.c_int64, VP, VP]),
         "lrtei_factors": (S, [VP, VP, VP, VP, VP, VP, VP]),
         "lrtei_jbuild": (S, [VP, VP, ctypes.c_int, VP, VP]),
         "lrtei_jbuild_batched": (S, [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(VP), IP, ctypes.POINTER(VP),
@@ -184,6 +185,12 @@ def lrtei_assemble_Bu_rows(plan: int, form: int, row_begin: int, row_end: int, d
 
 def lrtei_entries(plan: int, d_idx4, count: int, d_out, stream=None):
     _check(load().lrtei_entries(plan, _ptr(d_idx4), int(count), _ptr(d_out), _stream(stream)))
+
+
+def lrtei_entries_noalloc(plan: int, d_idx4, count: int, d_out, stream=None):
+    """Algorithm 1 entries without any device allocation (fixed 4 MiB scratch per device,
+    at most 262144 entries per call; calls that overlap on the GPU race on the scratch)."""
+    _check(load().lrtei_entries_noalloc(plan, _ptr(d_idx4), int(count), _ptr(d_out), _stream(stream)))
 
 
 def lrtei_factors(plan: int, d_S=None, d_C=None, d_s=None, d_w=None, d_c=None, stream=None):
