@@ -28,7 +28,12 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "lrtei_internal.h"
 
@@ -36,17 +41,21 @@ namespace lrtei {
 namespace tc {
 
 constexpr int BM = 128;      // rows of A per tile (MMA M)
-constexpr int BK = 64;       // K per pipeline stage (128-byte rows, 128B swizzle)
 constexpr int KCHUNK = 256;  // K per exact FP32 accumulation chunk
+// K per pipeline stage, BK: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte rows, 64-byte
+// swizzle, smaller stages so more of them fit in shared memory).
 constexpr int NA = 3;        // A slices: s0, t1, t2'
 constexpr int NB = 4;        // B slices: s0, t1, t1', t2'
 constexpr int kEpiWarps = 16;               // 4 per TMEM lane quadrant
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
+constexpr int kGroupM = 16;    // tiles of M walked together (L2 reuse of both operands)
+constexpr int kGroupRows = 8;  // block rows walked together in the symmetric upper triangle
+
 struct Params {
   int64_t M, N;
-  int64_t tiles_n;
+  int64_t tiles_m, tiles_n;
   int64_t ntiles;         // number of output tiles (upper triangle if symmetric)
   int nchunks_total;      // kpad / KCHUNK
   int chunks_per_split;
@@ -118,14 +127,17 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, void* dst, u
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// K-major operand tile with 128-byte swizzle: 8-row x 128-byte atoms, atoms 1024 bytes apart.
+// K-major operand tile with BK*2-byte rows and the matching swizzle: 8-row atoms of 8*BK*2
+// bytes stacked along M/N (128-byte swizzle for BK = 64, 64-byte swizzle for BK = 32).
+template <int BK>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  static_assert(BK == 64 || BK == 32, "BK");
   uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;                   // descriptor version
-  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((8 * BK * 2) >> 4) << 32;         // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;          // 128-byte or 64-byte swizzle
   return d;
 }
 
@@ -175,7 +187,7 @@ __device__ __forceinline__ double pow2(int k) {  // 2^k, exponent clamped to the
 
 // ------------------------------------------------------------------ the kernel
 // PLAIN: one BF16 operand plane each, one product per k step, FP32 sums (no exactness).
-template <int BN, int STAGES, bool PLAIN>
+template <int BN, int BK, int STAGES, bool PLAIN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
               const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
@@ -205,18 +217,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   // tile coordinates
   int64_t ti, tj;
   const int64_t tile = blockIdx.x;
+  // Tile order: the ~152 CTAs resident at once should share operand slabs in L2, so tiles are
+  // walked in groups of kGroupM M-tiles (M fastest inside a group).  The symmetric product walks
+  // the upper triangle of 128x128 blocks in groups of kGroupRows block rows, column by column.
   bool mirror_tile = false;
-  if (p.symmetric) {  // upper triangle of 128 x 128 blocks, each split into BM/BN column tiles
+  if (p.symmetric) {
     constexpr int SUB = BM / BN;
-    int64_t t = tile / SUB, r = 0, len = (p.tiles_n + SUB - 1) / SUB;
+    const int64_t nb = (p.tiles_n + SUB - 1) / SUB;  // 128x128 blocks per side
+    int64_t t = tile / SUB;
     const int sub = (int)(tile % SUB);
-    while (t >= len) { t -= len; ++r; --len; }
+    int64_t r = 0, c = 0;
+    for (int64_t R0 = 0; R0 < nb; R0 += kGroupRows) {
+      const int64_t R1 = min(nb, R0 + kGroupRows), g = R1 - R0;
+      const int64_t in_group = g * (g + 1) / 2 + (nb - R1) * g;
+      if (t >= in_group) { t -= in_group; continue; }
+      for (c = R0; c < nb; ++c) {
+        const int64_t rows_here = min(c, R1 - 1) - R0 + 1;
+        if (t < rows_here) { r = R0 + t; break; }
+        t -= rows_here;
+      }
+      break;
+    }
     ti = r;
-    tj = (r + t) * SUB + sub;
-    mirror_tile = (r + t) != r;  // strictly above the diagonal block: write the transpose too
+    tj = c * SUB + sub;
+    mirror_tile = c != r;  // strictly above the diagonal block: write the transpose too
   } else {
-    ti = tile / p.tiles_n;
-    tj = tile % p.tiles_n;
+    const int64_t per_group = (int64_t)kGroupM * p.tiles_n;
+    const int64_t first_m = (tile / per_group) * kGroupM;
+    const int64_t gsize = min((int64_t)kGroupM, p.tiles_m - first_m);
+    const int64_t in_g = tile % per_group;
+    ti = first_m + in_g % gsize;
+    tj = in_g / gsize;
   }
   const int64_t m0 = ti * BM, n0 = tj * BN;
   const int split = blockIdx.y;
@@ -298,11 +329,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1u, abort_flag, p.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
-          const uint64_t a0 = smem_desc(base), a1 = smem_desc(base + A_BYTES), a2 = smem_desc(base + 2 * A_BYTES);
+          const uint64_t a0 = smem_desc<BK>(base), a1 = smem_desc<BK>(base + A_BYTES),
+                         a2 = smem_desc<BK>(base + 2 * A_BYTES);
           const uint32_t bb = base + NA_ * A_BYTES;
-          const uint64_t b0 = smem_desc(bb), b1 = smem_desc(bb + B_BYTES), b1h = smem_desc(bb + 2 * B_BYTES),
-                         b2 = smem_desc(bb + 3 * B_BYTES);
-#pragma unroll 1
+          const uint64_t b0 = smem_desc<BK>(bb), b1 = smem_desc<BK>(bb + B_BYTES), b1h = smem_desc<BK>(bb + 2 * B_BYTES),
+                         b2 = smem_desc<BK>(bb + 3 * B_BYTES);
+#pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
             const uint64_t o = (uint64_t)((k * 32) >> 4);  // +32 bytes along K inside the swizzle atom
             const uint32_t first = (step == 0 && k == 0) ? 0u : 1u;
@@ -525,33 +557,38 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-static bool encode_plane(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t kpad, int box_rows, bool bf16) {
+static bool encode_plane(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t kpad, int box_rows, bool bf16,
+                         int bk) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(kpad * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool PLAIN>
+template <int BN, int BK, int STAGES, bool PLAIN>
 static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits,
                               cudaStream_t st) {
   CUtensorMap m[7];
   bool ok;
   if (PLAIN) {
-    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, true) && encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, true);
+    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, true, BK) && encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, true, BK);
     m[1] = m[2] = m[0];
     m[4] = m[5] = m[6] = m[3];
   } else {
-    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, false) && encode_plane(&m[1], A.s1, A.rows, A.kpad, BM, false) &&
-         encode_plane(&m[2], A.s2, A.rows, A.kpad, BM, false) && encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, false) &&
-         encode_plane(&m[4], B.s1, B.rows, B.kpad, BN, false) && encode_plane(&m[5], B.s1h, B.rows, B.kpad, BN, false) &&
-         encode_plane(&m[6], B.s2, B.rows, B.kpad, BN, false);
+    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, false, BK) &&
+         encode_plane(&m[1], A.s1, A.rows, A.kpad, BM, false, BK) &&
+         encode_plane(&m[2], A.s2, A.rows, A.kpad, BM, false, BK) &&
+         encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, false, BK) &&
+         encode_plane(&m[4], B.s1, B.rows, B.kpad, BN, false, BK) &&
+         encode_plane(&m[5], B.s1h, B.rows, B.kpad, BN, false, BK) &&
+         encode_plane(&m[6], B.s2, B.rows, B.kpad, BN, false, BK);
   }
   if (!ok) {
     set_error("cuTensorMapEncodeTiled failed (driver entry point unavailable or bad operand layout)");
@@ -561,11 +598,11 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
   const size_t tile_bytes = (size_t)BM * (BN + 1) * 8 + (BM + BN) * 4;
   const size_t smem = std::max(STAGES * stage, tile_bytes) + 1024 + 256;
   cudaError_t e =
-      cudaFuncSetAttribute(k_tc_gemm<BN, STAGES, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_tc_gemm<BN, BK, STAGES, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "tc_gemm smem attribute");
   dim3 grid((unsigned)p.ntiles, (unsigned)splits);
   count_launch();
-  k_tc_gemm<BN, STAGES, PLAIN><<<grid, kThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);
+  k_tc_gemm<BN, BK, STAGES, PLAIN><<<grid, kThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tc_gemm launch");
   return LRTEI_OK;
@@ -602,6 +639,78 @@ void launch_reduce_splits(const double* part, int splits, int64_t stride, int64_
   count_launch();
   tc::k_reduce_splits<<<(unsigned)b, 256, 0, st>>>(part, splits, stride, rows, cols, ld, out, ldo);
 }
+
+namespace tc {
+// Kernel configurations (BN, BK, stages) the tuner chooses from.
+struct Config {
+  int bn, bk, stages;
+};
+static const Config kSplitCfg64[] = {{64, 64, 2}, {64, 32, 5}};
+static const Config kSplitCfg32[] = {{32, 64, 3}, {32, 32, 6}};
+static const Config kPlainCfg64[] = {{64, 64, 6}, {64, 32, 8}};
+static const Config kPlainCfg32[] = {{32, 64, 6}, {32, 32, 8}};
+
+static lrtei_status launch_cfg(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits, bool plain,
+                               const Config& c, cudaStream_t st) {
+  if (plain) {
+    if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 6, true>(A, B, p, splits, st)
+                                      : launch_tc<64, 32, 8, true>(A, B, p, splits, st);
+    return c.bk == 64 ? launch_tc<32, 64, 6, true>(A, B, p, splits, st) : launch_tc<32, 32, 8, true>(A, B, p, splits, st);
+  }
+  if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 2, false>(A, B, p, splits, st)
+                                    : launch_tc<64, 32, 5, false>(A, B, p, splits, st);
+  return c.bk == 64 ? launch_tc<32, 64, 3, false>(A, B, p, splits, st) : launch_tc<32, 32, 6, false>(A, B, p, splits, st);
+}
+
+// Tuning cache: one entry per GEMM shape class; filled the first time a shape is seen outside
+// stream capture by timing every candidate once (each candidate writes the full, correct C).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int>, int> g_tune;
+
+static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits, int BN,
+                              bool plain, cudaStream_t st) {
+  const Config* cands = plain ? (BN == 64 ? kPlainCfg64 : kPlainCfg32) : (BN == 64 ? kSplitCfg64 : kSplitCfg32);
+  const int ncand = 2;
+  const char* force = getenv("LRTEI_TC_CONFIG");
+  if (force && *force) {
+    const int i = atoi(force);
+    ProfScope ps("tc_gemm", st);
+    return launch_cfg(A, B, p, splits, plain, cands[(i < 0 || i >= ncand) ? 0 : i], st);
+  }
+  const auto key = std::make_tuple(p.M, p.N, A.kpad, splits, (int)plain, p.symmetric, p.transpose_out);
+  int choice = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) choice = it->second;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (choice < 0 && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "tune events");
+    for (int i = 0; i < ncand; ++i) {
+      cudaEventRecord(e0, st);
+      lrtei_status s = launch_cfg(A, B, p, splits, plain, cands[i], st);
+      if (s != LRTEI_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+      cudaEventRecord(e1, st);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(e, "tune sync"); }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; choice = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = choice;
+    return LRTEI_OK;  // C holds the last candidate's (correct) result
+  }
+  if (choice < 0) choice = 0;
+  ProfScope ps("tc_gemm", st);
+  return launch_cfg(A, B, p, splits, plain, cands[choice], st);
+}
+}  // namespace tc
 
 // C = scale * A B^T.  A: M rows (slices s0,s1,s2), B: N rows (slices s0,s1,s1h,s2), same kpad
 // (multiple of 256, <= 32768 per split).  d_C: FP64, ldc; transpose_out writes C^T.
@@ -640,6 +749,7 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
   // register file share of the epilogue warps.
   const int BN = (N <= 32) ? 32 : 64;
   const int64_t tiles_m = (M + tc::BM - 1) / tc::BM, tiles_n = (N + BN - 1) / BN;
+  p.tiles_m = tiles_m;
   p.tiles_n = tiles_n;
   if (symmetric_upper) {
     // upper-triangular enumeration in units of 128 x 128 blocks, each done as two 128 x 64 tiles
@@ -660,19 +770,12 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
     p.ldc = ldc;
     p.split_stride = 0;
   }
-  lrtei_status s;
-  {
-    ProfScope ps("tc_gemm", st);
-    const bool plain = A.plain;
-    if (plain != B.plain) {
-      set_error("tc_gemm: operands must both be plain or both split");
-      return LRTEI_ERR_ARG;
-    }
-    if (BN == 64)
-      s = plain ? tc::launch_tc<64, 4, true>(A, B, p, splits, st) : tc::launch_tc<64, 2, false>(A, B, p, splits, st);
-    else
-      s = plain ? tc::launch_tc<32, 4, true>(A, B, p, splits, st) : tc::launch_tc<32, 3, false>(A, B, p, splits, st);
+  const bool plain = A.plain;
+  if (plain != B.plain) {
+    set_error("tc_gemm: operands must both be plain or both split");
+    return LRTEI_ERR_ARG;
   }
+  lrtei_status s = tc::run_tuned(A, B, p, splits, BN, plain, st);
   if (s != LRTEI_OK) return s;
   if (splits > 1) {
     if (transpose_out)
