@@ -269,3 +269,22 @@ def test_split_f16_full_size_180(lib):
     err = float(torch.linalg.norm(J - J64) / torch.linalg.norm(J64))
     print(f"split_f16 J-build, 180 functions, 32 densities: rel. error vs FP64 {err:.3e}")
     assert err <= 1e-7
+
+
+@pytest.mark.parametrize("cfg", ["0", "1"])
+def test_split_f16_each_tile_config(lib, cfg, monkeypatch):
+    """Every kernel configuration the tuner may pick (64- and 32-deep K stages, 128x64 and
+    128x32 tiles) gives the same accuracy on B and J."""
+    import torch
+    monkeypatch.setenv("LRTEI_TC_CONFIG", cfg)
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    ref = o.assemble_B()
+    pl = lib.Plan(m, "split_f16")
+    B = pl.assemble_B().cpu().numpy()
+    pl.status()
+    assert rel_fro(B, ref) <= 1e-7
+    assert np.array_equal(B, B.T)
+    D = synth.random_densities(13, m.nbf, 40)
+    J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+    assert rel_fro(J, o.jbuild_factored(D)) <= 1e-7
