@@ -597,9 +597,13 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
   constexpr size_t stage = (size_t)(PLAIN ? 1 : NA) * BM * BK * 2 + (size_t)(PLAIN ? 1 : NB) * BN * BK * 2;
   const size_t tile_bytes = (size_t)BM * (BN + 1) * 8 + (BM + BN) * 4;
   const size_t smem = std::max(STAGES * stage, tile_bytes) + 1024 + 256;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_tc_gemm<BN, BK, STAGES, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "tc_gemm smem attribute");
+  static bool attr_set = false;  // once per instantiation (also keeps it out of stream capture)
+  cudaError_t e = cudaSuccess;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(k_tc_gemm<BN, BK, STAGES, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "tc_gemm smem attribute");
+    attr_set = true;
+  }
   dim3 grid((unsigned)p.ntiles, (unsigned)splits);
   count_launch();
   k_tc_gemm<BN, BK, STAGES, PLAIN><<<grid, kThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);

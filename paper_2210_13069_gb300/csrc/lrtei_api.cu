@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -102,6 +104,8 @@ struct lrtei_plan {
     for (void* q : allocs) cudaFree(q);
   }
 };
+
+static void forget_plan_graphs(const lrtei_plan* pl);
 
 #define LRTEI_TRY(expr)                    \
   do {                                     \
@@ -325,6 +329,7 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
 void lrtei_plan_destroy(lrtei_plan* plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
+  forget_plan_graphs(plan);
   delete plan;
 }
 
@@ -424,17 +429,42 @@ lrtei_status alloc_split(lrtei_plan* pl, SplitMatrix& m, int64_t rows, int64_t k
   return LRTEI_OK;
 }
 
-lrtei_status ensure_Fsp(lrtei_plan* pl, cudaStream_t st) {
-  if (pl->have_Fsp) return LRTEI_OK;
+void release_split(lrtei_plan* pl, SplitMatrix& m) {
+  const size_t b = (size_t)m.rows * m.kpad * sizeof(uint16_t);
+  pl->release(m.s0, b);
+  pl->release(m.s1, b);
+  pl->release(m.s2, b);
+  pl->release(m.s1h, b);
+  pl->release(m.expo, (size_t)m.rows * sizeof(int));
+  m = SplitMatrix();
+}
+
+// F_u slices.  The fourth plane (t1 / 2^11) is only needed when F_u is the B operand (the
+// assembly B_u = G F_u^T); J-builds use F_u as the A operand only.
+lrtei_status ensure_Fsp(lrtei_plan* pl, cudaStream_t st, bool need_s1h) {
+  if (pl->have_Fsp && (!need_s1h || pl->Fsp.plain || pl->Fsp.s1h)) return LRTEI_OK;
+  if (pl->have_Fsp) {
+    release_split(pl, pl->Fsp);
+    pl->have_Fsp = false;
+  }
   const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
   LRTEI_TRY(ensure_F64(pl, st));
-  LRTEI_TRY(alloc_split(pl, pl->Fsp, pl->t.npair, n3, true));
+  LRTEI_TRY(alloc_split(pl, pl->Fsp, pl->t.npair, n3, need_s1h));
   {
     ProfScope ps("split", st);
-    launch_split_rows(pl->d_F, pl->t.npair, n3, n3, pl->Fsp, true, nslices(pl), st);
+    launch_split_rows(pl->d_F, pl->t.npair, n3, n3, pl->Fsp, need_s1h, nslices(pl), st);
   }
   pl->have_Fsp = true;
   return finish_launch("split F");
+}
+
+// A split-precision plan keeps no FP64 copy of F_u once both slice layouts exist.
+void drop_F64_if_sliced(lrtei_plan* pl, cudaStream_t st) {
+  if (!is_split(pl) || !pl->d_F || !pl->have_Fsp || !pl->have_FTsp) return;
+  cudaStreamSynchronize(st);  // the slicing kernels read d_F
+  const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
+  pl->release(pl->d_F, sizeof(double) * (size_t)pl->t.npair * n3);
+  pl->d_F = nullptr;
 }
 
 // Scratch buffer owned by the call (freed at the end of the call, stream-ordered).
@@ -460,17 +490,23 @@ struct Scratch {
   }
 };
 
-lrtei_status ensure_Ksp(lrtei_plan* pl, cudaStream_t st) {
-  if (pl->have_Ksp) return LRTEI_OK;
+// Dense K = sum_p w_p A_x^p (x) A_y^p (x) A_z^p as slices; the fourth plane only when K is the
+// B operand (G = F_u K); the J-build uses K as the A operand.
+lrtei_status ensure_Ksp(lrtei_plan* pl, cudaStream_t st, bool need_s1h) {
+  if (pl->have_Ksp && (!need_s1h || pl->Ksp.plain || pl->Ksp.s1h)) return LRTEI_OK;
+  if (pl->have_Ksp) {
+    release_split(pl, pl->Ksp);
+    pl->have_Ksp = false;
+  }
   const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
   Scratch sc(st);
   double* K;
   LRTEI_TRY(sc.get(&K, (size_t)n3 * n3));
   launch_build_K(pl->n, pl->P, pl->d_C, pl->d_w, K, st);
-  LRTEI_TRY(alloc_split(pl, pl->Ksp, n3, n3, true));
+  LRTEI_TRY(alloc_split(pl, pl->Ksp, n3, n3, need_s1h));
   {
     ProfScope ps("split", st);
-    launch_split_rows(K, n3, n3, n3, pl->Ksp, true, nslices(pl), st);
+    launch_split_rows(K, n3, n3, n3, pl->Ksp, need_s1h, nslices(pl), st);
   }
   pl->have_Ksp = true;
   return finish_launch("split K");
@@ -491,6 +527,15 @@ lrtei_status ensure_FTsp(lrtei_plan* pl, cudaStream_t st) {
   }
   pl->have_FTsp = true;
   return finish_launch("split F^T");
+}
+
+// Operands of the tensor-core J-build: F_u^T and F_u (A operands) and K (A operand).
+lrtei_status ensure_jbuild_operands(lrtei_plan* pl, cudaStream_t st) {
+  LRTEI_TRY(ensure_FTsp(pl, st));
+  LRTEI_TRY(ensure_Fsp(pl, st, false));
+  LRTEI_TRY(ensure_Ksp(pl, st, false));
+  drop_F64_if_sliced(pl, st);
+  return LRTEI_OK;
 }
 
 // A scratch split operand (planes owned by the call).
@@ -520,8 +565,8 @@ int splits_for(int64_t M, int64_t K) {
 lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int64_t ld, cudaStream_t st) {
   const double pref = pl->omega / sqrt(3.14159265358979323846);
   const int64_t n3 = (int64_t)pl->n * pl->n * pl->n, npair = pl->t.npair, nr = r1 - r0;
-  LRTEI_TRY(ensure_Fsp(pl, st));
-  LRTEI_TRY(ensure_Ksp(pl, st));
+  LRTEI_TRY(ensure_Fsp(pl, st, true));
+  LRTEI_TRY(ensure_Ksp(pl, st, true));
   Scratch sc(st);
   double* G;
   LRTEI_TRY(sc.get(&G, (size_t)nr * n3));
@@ -603,6 +648,117 @@ lrtei_status bu_rows(lrtei_plan* pl, int form, int64_t r0, int64_t r1, double* o
 }
 
 }  // namespace
+
+namespace {
+// Captured batches: one CUDA graph per (plans, densities, outputs, R) set.  Molecules are spread
+// over kSideStreams capture streams so that the kernels of small molecules run concurrently.
+constexpr int kSideStreams = 4;
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+std::mutex g_batch_mu;
+std::map<std::vector<uintptr_t>, BatchGraph> g_batch;
+
+lrtei_status capture_batch(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,
+                           double* const* d_J, cudaStream_t st, BatchGraph* out) {
+  (void)st;  // the graph is captured on a stream of its own and launched later on the caller's
+  cudaStream_t origin, side[kSideStreams];
+  cudaEvent_t fork, join[kSideStreams];
+  LRTEI_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+  for (int i = 0; i < kSideStreams; ++i) LRTEI_CUDA(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
+  LRTEI_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (int i = 0; i < kSideStreams; ++i) LRTEI_CUDA(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+  const long long count0 = launch_count();
+  lrtei_status status = LRTEI_OK;
+  cudaGraph_t graph = nullptr;
+  LRTEI_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+  cudaEventRecord(fork, origin);
+  for (int i = 0; i < kSideStreams; ++i) cudaStreamWaitEvent(side[i], fork, 0);
+  for (int m = 0; m < nmol && status == LRTEI_OK; ++m)
+    status = lrtei_jbuild(plans[m], d_D[m], R[m], d_J[m], side[m % kSideStreams]);
+  for (int i = 0; i < kSideStreams; ++i) {
+    cudaEventRecord(join[i], side[i]);
+    cudaStreamWaitEvent(origin, join[i], 0);
+  }
+  cudaError_t e = cudaStreamEndCapture(origin, &graph);
+  set_launch_count(count0);
+  if (status == LRTEI_OK && e != cudaSuccess) status = cuda_fail(e, "batched J-build capture");
+  if (status == LRTEI_OK) {
+    e = cudaGraphInstantiate(&out->exec, graph, 0);
+    if (e != cudaSuccess) status = cuda_fail(e, "batched J-build instantiate");
+  }
+  if (status == LRTEI_OK) {
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++out->kernels;
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventDestroy(fork);
+  for (int i = 0; i < kSideStreams; ++i) {
+    cudaEventDestroy(join[i]);
+    cudaStreamDestroy(side[i]);
+  }
+  cudaStreamDestroy(origin);
+  cudaGetLastError();
+  return status;
+}
+
+lrtei_status batched_graph_run(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,
+                               double* const* d_J, cudaStream_t st) {
+  // operands of every molecule exist before capture (their set-up allocates and synchronises)
+  for (int m = 0; m < nmol; ++m) {
+    if (is_split(plans[m])) LRTEI_TRY(ensure_jbuild_operands(plans[m], st));
+    else LRTEI_TRY(ensure_F64(plans[m], st));
+  }
+  std::vector<uintptr_t> key;
+  key.push_back((uintptr_t)nmol);
+  for (int m = 0; m < nmol; ++m) {
+    key.push_back((uintptr_t)plans[m]);
+    key.push_back((uintptr_t)d_D[m]);
+    key.push_back((uintptr_t)d_J[m]);
+    key.push_back((uintptr_t)R[m]);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batch.find(key);
+    if (it != g_batch.end()) {
+      ProfScope ps("batched", st);
+      LRTEI_CUDA(cudaGraphLaunch(it->second.exec, st));
+      count_launches(it->second.kernels);
+      return LRTEI_OK;
+    }
+  }
+  // First call for this set: run it directly (this also settles the GEMM tuning choices for
+  // every shape), then capture the same work into a graph for the calls that follow.
+  for (int m = 0; m < nmol; ++m) LRTEI_TRY(lrtei_jbuild(plans[m], d_D[m], R[m], d_J[m], st));
+  BatchGraph g;
+  LRTEI_TRY(capture_batch(plans, nmol, d_D, R, d_J, st, &g));
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  g_batch[key] = g;
+  return LRTEI_OK;
+}
+}  // namespace
+
+// Captured batches that involve a plan are dropped when the plan is destroyed.
+static void forget_plan_graphs(const lrtei_plan* pl) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto it = g_batch.begin(); it != g_batch.end();) {
+    bool uses = false;
+    for (size_t i = 1; i < it->first.size(); i += 4) uses |= (it->first[i] == (uintptr_t)pl);
+    if (uses) {
+      cudaGraphExecDestroy(it->second.exec);
+      it = g_batch.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
 
 extern "C" {
 
@@ -688,9 +844,7 @@ static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double
   const int nbf = plan->basis.nbf, n = plan->n;
   const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;
   const double pref = plan->omega / sqrt(kPi);
-  LRTEI_TRY(ensure_Fsp(plan, st));
-  LRTEI_TRY(ensure_Ksp(plan, st));
-  LRTEI_TRY(ensure_FTsp(plan, st));
+  LRTEI_TRY(ensure_jbuild_operands(plan, st));
   Scratch sc(st);
   double *Du, *DuT, *XT, *YT, *Ju, *part;
   LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
@@ -768,8 +922,17 @@ lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_
 lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,
                                   double* const* d_J, void* stream) {
   if (!plans || nmol <= 0 || !d_D || !R || !d_J) { set_error("invalid batched arguments"); return LRTEI_ERR_ARG; }
-  for (int m = 0; m < nmol; ++m) LRTEI_TRY(lrtei_jbuild(plans[m], d_D[m], R[m], d_J[m], stream));
-  return LRTEI_OK;
+  for (int m = 0; m < nmol; ++m) {
+    if (!plans[m] || !d_D[m] || !d_J[m] || R[m] <= 0) {
+      set_error("batched J-build: molecule %d has a NULL plan/pointer or R <= 0", m);
+      return LRTEI_ERR_ARG;
+    }
+    if (is_split(plans[m]) != is_split(plans[0])) {
+      set_error("batched J-build: all plans must use tensor-core or all CUDA-core precision");
+      return LRTEI_ERR_ARG;
+    }
+  }
+  return batched_graph_run(plans, nmol, d_D, R, d_J, (cudaStream_t)stream);
 }
 
 }  // extern "C"

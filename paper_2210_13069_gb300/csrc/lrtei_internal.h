@@ -31,6 +31,9 @@ lrtei_status cuda_fail(cudaError_t e, const char* what);
 
 // Counts kernel launches made by the library (reported by lrtei_profile_get("*")).
 void count_launch();
+void count_launches(long long n);
+long long launch_count();
+void set_launch_count(long long n);
 
 // Kernel timing: events recorded on the launching stream when profiling is enabled.
 struct ProfScope {

@@ -19,9 +19,14 @@ bool g_on = false;
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
+void set_launch_count(long long n) { g_launches.store(n); }
 
 ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), st(s) {
   if (!g_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
     cudaGetLastError();
     a = b = nullptr;
