@@ -1,27 +1,318 @@
-// k_mlp.cu -- the learned (n, P) selector: a 3-layer FP32 MLP with hand-written forward,
-// backward and Adam kernels.
+// k_mlp.cu -- the learned (n, P) selector: a 3-layer FP32 MLP (6 -> H -> H -> 2, ReLU) with
+// hand-written forward, backward (mean squared error) and Adam kernels.
+//
+// Parameters are packed W1 (H x 6), b1 (H), W2 (H x H), b2 (H), W3 (2 x H), b3 (2), row-major,
+// and live on the device.  One thread evaluates one sample; the weights are staged in shared
+// memory; gradients are reduced per block in shared memory and added to the global gradient
+// with one atomic per parameter per block.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "lrtei_internal.h"
+
+namespace lrtei {
+namespace mlp {
+
+constexpr int kIn = 6, kOut = 2, kMaxH = 64, kThreads = 128;
+
+__host__ __device__ inline int64_t nparams(int H) { return (int64_t)H * kIn + H + (int64_t)H * H + H + kOut * H + kOut; }
+
+struct Off {
+  int w1, b1, w2, b2, w3, b3;
+};
+__host__ __device__ inline Off offsets(int H) {
+  Off o;
+  o.w1 = 0;
+  o.b1 = o.w1 + H * kIn;
+  o.w2 = o.b1 + H;
+  o.b2 = o.w2 + H * H;
+  o.w3 = o.b2 + H;
+  o.b3 = o.w3 + kOut * H;
+  return o;
+}
+
+__device__ inline void forward_one(const float* __restrict__ w, const Off& o, int H, const float* x, float* h1,
+                                   float* h2, float* y) {
+  for (int j = 0; j < H; ++j) {
+    float a = w[o.b1 + j];
+    for (int i = 0; i < kIn; ++i) a += w[o.w1 + j * kIn + i] * x[i];
+    h1[j] = a > 0.f ? a : 0.f;
+  }
+  for (int j = 0; j < H; ++j) {
+    float a = w[o.b2 + j];
+    for (int k = 0; k < H; ++k) a += w[o.w2 + j * H + k] * h1[k];
+    h2[j] = a > 0.f ? a : 0.f;
+  }
+  for (int q = 0; q < kOut; ++q) {
+    float a = w[o.b3 + q];
+    for (int k = 0; k < H; ++k) a += w[o.w3 + q * H + k] * h2[k];
+    y[q] = a;
+  }
+}
+
+__global__ void k_forward(const float* __restrict__ params, int H, const float* __restrict__ X, int N,
+                          float* __restrict__ Y) {
+  extern __shared__ float sw[];
+  const int64_t np = nparams(H);
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) sw[t] = params[t];
+  __syncthreads();
+  const Off o = offsets(H);
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  float x[kIn], h1[kMaxH], h2[kMaxH], y[kOut];
+  for (int i = 0; i < kIn; ++i) x[i] = X[(int64_t)s * kIn + i];
+  forward_one(sw, o, H, x, h1, h2, y);
+  for (int q = 0; q < kOut; ++q) Y[(int64_t)s * kOut + q] = y[q];
+}
+
+// Gradient of L = (1 / (N kOut)) sum_s sum_q (y_sq - t_sq)^2 over the rows idx[0..n) (or 0..n).
+__global__ void k_backward(const float* __restrict__ params, int H, const float* __restrict__ X,
+                           const float* __restrict__ T, const int* __restrict__ idx, int n, float inv_count,
+                           float* __restrict__ grad, float* __restrict__ loss) {
+  extern __shared__ float sm[];
+  const int64_t np = nparams(H);
+  float* sw = sm;
+  float* sg = sm + np;
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+    sw[t] = params[t];
+    sg[t] = 0.f;
+  }
+  __syncthreads();
+  const Off o = offsets(H);
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (b < n) {
+    const int64_t s = idx ? idx[b] : b;
+    float x[kIn], h1[kMaxH], h2[kMaxH], y[kOut], dy[kOut];
+    for (int i = 0; i < kIn; ++i) x[i] = X[s * kIn + i];
+    forward_one(sw, o, H, x, h1, h2, y);
+    for (int q = 0; q < kOut; ++q) {
+      const float d = y[q] - T[s * kOut + q];
+      l += d * d;
+      dy[q] = 2.f * d * inv_count;
+      atomicAdd(&sg[o.b3 + q], dy[q]);
+      for (int k = 0; k < H; ++k) atomicAdd(&sg[o.w3 + q * H + k], dy[q] * h2[k]);
+    }
+    // dh2 (reuse h2 storage after its use above): dh2_k = sum_q W3[q][k] dy_q, masked by ReLU
+    for (int k = 0; k < H; ++k) {
+      float a = 0.f;
+      for (int q = 0; q < kOut; ++q) a += sw[o.w3 + q * H + k] * dy[q];
+      h2[k] = h2[k] > 0.f ? a : 0.f;
+    }
+    for (int j = 0; j < H; ++j) {
+      atomicAdd(&sg[o.b2 + j], h2[j]);
+      for (int k = 0; k < H; ++k) atomicAdd(&sg[o.w2 + j * H + k], h2[j] * h1[k]);
+    }
+    // dh1_k = sum_j W2[j][k] dh2_j, masked by ReLU
+    float dh1[kMaxH];
+    for (int k = 0; k < H; ++k) {
+      float a = 0.f;
+      for (int j = 0; j < H; ++j) a += sw[o.w2 + j * H + k] * h2[j];
+      dh1[k] = h1[k] > 0.f ? a : 0.f;
+    }
+    for (int j = 0; j < H; ++j) {
+      atomicAdd(&sg[o.b1 + j], dh1[j]);
+      for (int i = 0; i < kIn; ++i) atomicAdd(&sg[o.w1 + j * kIn + i], dh1[j] * x[i]);
+    }
+  }
+  // block loss
+  for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l * inv_count);
+  __syncthreads();
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x)
+    if (sg[t] != 0.f) atomicAdd(&grad[t], sg[t]);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t np, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+}  // namespace mlp
+}  // namespace lrtei
 
 struct lrtei_selector {
   int hidden = 64;
+  int64_t np = 0;
+  float* d_params = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  float* d_grad = nullptr;
+  float* d_loss = nullptr;
+  int* d_idx = nullptr;
+  int idx_cap = 0;
+  int64_t step = 0;
+  uint64_t rng = 0;
 };
 
+namespace {
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+double uniform01(uint64_t& s) { return (splitmix64(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+size_t smem_fwd(int H) { return sizeof(float) * lrtei::mlp::nparams(H); }
+size_t smem_bwd(int H) { return 2 * sizeof(float) * lrtei::mlp::nparams(H); }
+}  // namespace
+
 extern "C" {
+
 lrtei_status lrtei_selector_create(int hidden, uint64_t seed, lrtei_selector** out) {
-  (void)hidden; (void)seed;
-  if (out) *out = nullptr;
-  lrtei::set_error("selector not built yet");
-  return LRTEI_ERR_UNSUPPORTED;
+  using namespace lrtei;
+  if (!out) { set_error("out is NULL"); return LRTEI_ERR_ARG; }
+  *out = nullptr;
+  if (hidden < 1 || hidden > mlp::kMaxH) { set_error("hidden width must be in 1..%d", mlp::kMaxH); return LRTEI_ERR_ARG; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    set_error("no CUDA device available");
+    return LRTEI_ERR_CUDA;
+  }
+  lrtei_selector* s = new lrtei_selector();
+  s->hidden = hidden;
+  s->np = mlp::nparams(hidden);
+  s->rng = seed;
+  // He-uniform initialisation from a counter-based generator (splitmix64)
+  std::vector<float> h(s->np, 0.f);
+  const mlp::Off o = mlp::offsets(hidden);
+  auto fill = [&](int off, int count, int fan_in) {
+    const double a = sqrt(6.0 / fan_in);
+    for (int i = 0; i < count; ++i) h[off + i] = (float)((2.0 * uniform01(s->rng) - 1.0) * a);
+  };
+  fill(o.w1, hidden * mlp::kIn, mlp::kIn);
+  fill(o.w2, hidden * hidden, hidden);
+  fill(o.w3, mlp::kOut * hidden, hidden);
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->d_params, sizeof(float) * s->np)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_m, sizeof(float) * s->np)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_v, sizeof(float) * s->np)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_grad, sizeof(float) * s->np)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_loss, sizeof(float))) != cudaSuccess) {
+    lrtei_selector_destroy(s);
+    return cuda_fail(e, "selector allocation");
+  }
+  cudaMemcpy(s->d_params, h.data(), sizeof(float) * s->np, cudaMemcpyHostToDevice);
+  cudaMemset(s->d_m, 0, sizeof(float) * s->np);
+  cudaMemset(s->d_v, 0, sizeof(float) * s->np);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    lrtei_selector_destroy(s);
+    return cuda_fail(e, "selector init");
+  }
+  *out = s;
+  return LRTEI_OK;
 }
-void lrtei_selector_destroy(lrtei_selector* sel) { delete sel; }
-lrtei_status lrtei_selector_train_epoch(lrtei_selector*, const float*, const float*, int, int, float, float*, void*) {
-  return LRTEI_ERR_UNSUPPORTED;
+
+void lrtei_selector_destroy(lrtei_selector* s) {
+  if (!s) return;
+  cudaFree(s->d_params);
+  cudaFree(s->d_m);
+  cudaFree(s->d_v);
+  cudaFree(s->d_grad);
+  cudaFree(s->d_loss);
+  cudaFree(s->d_idx);
+  delete s;
 }
-lrtei_status lrtei_selector_forward(lrtei_selector*, const float*, float*, int, void*) { return LRTEI_ERR_UNSUPPORTED; }
-lrtei_status lrtei_selector_grad(lrtei_selector*, const float*, const float*, int, float*, float*, void*) {
-  return LRTEI_ERR_UNSUPPORTED;
+
+int64_t lrtei_selector_nparams(const lrtei_selector* s) { return s ? s->np : 0; }
+
+lrtei_status lrtei_selector_forward(lrtei_selector* s, const float* d_X, float* d_Yhat, int N, void* stream) {
+  using namespace lrtei;
+  if (!s || N < 0 || (N > 0 && (!d_X || !d_Yhat))) { set_error("invalid selector forward arguments"); return LRTEI_ERR_ARG; }
+  if (N == 0) return LRTEI_OK;
+  count_launch();
+  mlp::k_forward<<<(N + mlp::kThreads - 1) / mlp::kThreads, mlp::kThreads, smem_fwd(s->hidden), (cudaStream_t)stream>>>(
+      s->d_params, s->hidden, d_X, N, d_Yhat);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LRTEI_OK : cuda_fail(e, "selector forward");
 }
-int64_t lrtei_selector_nparams(const lrtei_selector*) { return 0; }
-lrtei_status lrtei_selector_get_params(const lrtei_selector*, float*) { return LRTEI_ERR_UNSUPPORTED; }
-lrtei_status lrtei_selector_set_params(lrtei_selector*, const float*) { return LRTEI_ERR_UNSUPPORTED; }
+
+lrtei_status lrtei_selector_grad(lrtei_selector* s, const float* d_X, const float* d_Y, int N, float* d_grad, float* loss,
+                                 void* stream) {
+  using namespace lrtei;
+  if (!s || N <= 0 || !d_X || !d_Y || !d_grad) { set_error("invalid selector grad arguments"); return LRTEI_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  LRTEI_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(float) * s->np, st));
+  LRTEI_CUDA(cudaMemsetAsync(s->d_loss, 0, sizeof(float), st));
+  count_launch();
+  mlp::k_backward<<<(N + mlp::kThreads - 1) / mlp::kThreads, mlp::kThreads, smem_bwd(s->hidden), st>>>(
+      s->d_params, s->hidden, d_X, d_Y, nullptr, N, 1.f / (float)(N * mlp::kOut), d_grad, s->d_loss);
+  LRTEI_CUDA(cudaGetLastError());
+  if (loss) {
+    LRTEI_CUDA(cudaMemcpyAsync(loss, s->d_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    LRTEI_CUDA(cudaStreamSynchronize(st));
+  }
+  return LRTEI_OK;
 }
+
+lrtei_status lrtei_selector_train_epoch(lrtei_selector* s, const float* d_X, const float* d_Y, int N, int batch, float lr,
+                                        float* loss, void* stream) {
+  using namespace lrtei;
+  if (!s || N <= 0 || batch <= 0 || !d_X || !d_Y || !(lr > 0.f)) { set_error("invalid selector train arguments"); return LRTEI_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s->idx_cap < N) {
+    cudaFree(s->d_idx);
+    s->d_idx = nullptr;
+    LRTEI_CUDA(cudaMalloc(&s->d_idx, sizeof(int) * N));
+    s->idx_cap = N;
+  }
+  // a fresh permutation of the rows for this epoch (Fisher-Yates on the host, splitmix64)
+  std::vector<int> perm(N);
+  for (int i = 0; i < N; ++i) perm[i] = i;
+  for (int i = N - 1; i > 0; --i) {
+    const int j = (int)(splitmix64(s->rng) % (uint64_t)(i + 1));
+    std::swap(perm[i], perm[j]);
+  }
+  LRTEI_CUDA(cudaMemcpyAsync(s->d_idx, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  LRTEI_CUDA(cudaMemsetAsync(s->d_loss, 0, sizeof(float), st));
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  int nb = 0;
+  for (int off = 0; off < N; off += batch, ++nb) {
+    const int n = std::min(batch, N - off);
+    LRTEI_CUDA(cudaMemsetAsync(s->d_grad, 0, sizeof(float) * s->np, st));
+    count_launch();
+    mlp::k_backward<<<(n + mlp::kThreads - 1) / mlp::kThreads, mlp::kThreads, smem_bwd(s->hidden), st>>>(
+        s->d_params, s->hidden, d_X, d_Y, s->d_idx + off, n, 1.f / (float)(n * mlp::kOut), s->d_grad, s->d_loss);
+    ++s->step;
+    const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
+    count_launch();
+    mlp::k_adam<<<(int)((s->np + 255) / 256), 256, 0, st>>>(s->d_params, s->d_grad, s->d_m, s->d_v, s->np, lr, b1, b2,
+                                                            eps, c1, c2);
+  }
+  LRTEI_CUDA(cudaGetLastError());
+  if (loss) {
+    float l = 0.f;
+    LRTEI_CUDA(cudaMemcpyAsync(&l, s->d_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    LRTEI_CUDA(cudaStreamSynchronize(st));
+    *loss = l / (float)nb;  // mean over the epoch's mini-batches
+  }
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_selector_get_params(const lrtei_selector* s, float* h_params) {
+  using namespace lrtei;
+  if (!s || !h_params) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  LRTEI_CUDA(cudaMemcpy(h_params, s->d_params, sizeof(float) * s->np, cudaMemcpyDeviceToHost));
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_selector_set_params(lrtei_selector* s, const float* h_params) {
+  using namespace lrtei;
+  if (!s || !h_params) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  LRTEI_CUDA(cudaMemcpy(s->d_params, h_params, sizeof(float) * s->np, cudaMemcpyHostToDevice));
+  return LRTEI_OK;
+}
+
+}  // extern "C"

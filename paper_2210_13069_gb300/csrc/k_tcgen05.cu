@@ -100,10 +100,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: false if the CTA is aborting or the wait gave up (which raises the abort).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+// sleep_ns > 0 parks the waiting warp between polls, leaving issue slots to the MMA thread.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          unsigned sleep_ns = 0) {
   long long t0 = clock64();
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
+    if (sleep_ns) __nanosleep(sleep_ns);
     if ((++spins & 255u) == 0) {
       if (*abort_flag) return false;
       if (clock64() - t0 > kWaitCycles) {
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int it = 0; it < nk; ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status)) break;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, 32)) break;
         mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
         uint8_t* st = smem + (size_t)s * STAGE_BYTES;
         const int kx = (c_begin * KSTEPS + it) * BK;
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int buf = c & 1;
       // one lane waits, the warp reconverges before the .sync.aligned TMEM loads
       int got = 1;
-      if (lane == 0) got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, abort_flag, p.status) ? 1 : 0;
+      if (lane == 0) got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, abort_flag, p.status, 256) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) { ok = false; break; }
       tc_fence_after();

@@ -226,6 +226,56 @@ def lrtei_profile_get(kernel: str):
     return ms.value, cnt.value
 
 
+# ------------------------------------------------------------------ selector (MLP) calls
+
+FP = ctypes.POINTER(ctypes.c_float)
+
+
+def lrtei_selector_create(hidden: int = 64, seed: int = 1) -> int:
+    out = VP()
+    _check(load().lrtei_selector_create(int(hidden), int(seed), ctypes.byref(out)))
+    return out.value
+
+
+def lrtei_selector_destroy(sel: int):
+    load().lrtei_selector_destroy(sel)
+
+
+def lrtei_selector_nparams(sel: int) -> int:
+    return int(load().lrtei_selector_nparams(sel))
+
+
+def lrtei_selector_forward(sel: int, d_X, d_Yhat, N: int, stream=None):
+    _check(load().lrtei_selector_forward(sel, _ptr(d_X), _ptr(d_Yhat), int(N), _stream(stream)))
+
+
+def lrtei_selector_grad(sel: int, d_X, d_Y, N: int, d_grad, stream=None) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(load().lrtei_selector_grad(sel, _ptr(d_X), _ptr(d_Y), int(N), _ptr(d_grad), ctypes.byref(loss),
+                                      _stream(stream)))
+    return float(loss.value)
+
+
+def lrtei_selector_train_epoch(sel: int, d_X, d_Y, N: int, batch: int, lr: float, stream=None) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(load().lrtei_selector_train_epoch(sel, _ptr(d_X), _ptr(d_Y), int(N), int(batch), float(lr),
+                                             ctypes.byref(loss), _stream(stream)))
+    return float(loss.value)
+
+
+def lrtei_selector_get_params(sel: int) -> np.ndarray:
+    out = np.zeros(lrtei_selector_nparams(sel), dtype=np.float32)
+    _check(load().lrtei_selector_get_params(sel, out.ctypes.data_as(FP)))
+    return out
+
+
+def lrtei_selector_set_params(sel: int, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != lrtei_selector_nparams(sel):
+        raise LrteiError(1, "parameter count mismatch")
+    _check(load().lrtei_selector_set_params(sel, p.ctypes.data_as(FP)))
+
+
 def lrtei_last_error() -> str:
     return load().lrtei_last_error().decode()
 

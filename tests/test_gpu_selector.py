@@ -1,0 +1,103 @@
+"""The learned (n, P) selector: the device MLP kernels against the FP64 CPU reference network,
+training by the device Adam kernel, and the gain over the fixed (32, 48) on held-out instances.
+
+Training data are error sweeps of the plain method computed by the CUDA library; the held-out
+instances are drawn with different seeds.  The measured error of the chosen (n, P) on a
+held-out instance is that of the library's entries against the library's reference order.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as mlp_ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2210_13069_gb300 import build_lib, lrtei
+    assert torch.cuda.is_available()
+    build_lib.build()
+    lrtei.load()
+    return lrtei
+
+
+def test_mlp_forward_and_gradient_match_cpu_reference(lib):
+    import torch
+    H = 64
+    sel = lib.lrtei_selector_create(H, 5)
+    try:
+        theta = lib.lrtei_selector_get_params(sel).astype(np.float64)
+        rng = np.random.default_rng(1)
+        X = rng.normal(0, 1, (777, 6)).astype(np.float32)
+        T = rng.normal(0, 1, (777, 2)).astype(np.float32)
+        dX, dT = torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda")
+        out = torch.empty((777, 2), dtype=torch.float32, device="cuda")
+        lib.lrtei_selector_forward(sel, dX, out, 777)
+        y_ref = mlp_ref.forward(theta, H, X.astype(np.float64))
+        assert np.max(np.abs(out.cpu().numpy() - y_ref)) <= 1e-4 * max(1.0, np.abs(y_ref).max())
+        g = torch.empty(lib.lrtei_selector_nparams(sel), dtype=torch.float32, device="cuda")
+        loss = lib.lrtei_selector_grad(sel, dX, dT, 777, g)
+        L_ref, g_ref = mlp_ref.loss_and_grad(theta, H, X.astype(np.float64), T.astype(np.float64))
+        assert abs(loss - L_ref) <= 1e-5 * L_ref
+        gg = g.cpu().numpy()
+        assert np.linalg.norm(gg - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    finally:
+        lib.lrtei_selector_destroy(sel)
+
+
+def test_adam_training_fits_a_smooth_map(lib):
+    from paper_2210_13069_gb300.selector import Selector
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, (4096, 6)).astype(np.float32)
+    Y = np.stack([0.5 * np.sin(X[:, 0] * 2) + 0.2 * X[:, 1] * X[:, 2], 0.3 * X[:, 3] ** 2 - 0.1 * X[:, 4]], 1)
+    s = Selector(64, seed=3)
+    hist = s.train(X, Y.astype(np.float32), epochs=120, batch=256, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+    assert hist[-1] < 2e-3
+
+
+def test_selector_meets_target_and_gains_over_fixed(lib, tmp_path):
+    """Train on sweeps, then on held-out instances: the chosen (n, P) reaches the requested error
+    in at least 90 % of the reachable cases, and where the fixed (32, 48) also reaches it the
+    chosen one is cheaper on average (cost ~ n^3 per J-build)."""
+    import torch
+    from paper_2210_13069_gb300 import selector as S
+    train = [S.sweep(10_000 + i) for i in range(260)]
+    X, Y = S.dataset(train)
+    assert len(X) > 600
+    sel = S.Selector(64, seed=11)
+    hist = sel.train(X, Y, epochs=250, batch=256, lr=2e-3)
+    assert hist[-1] < hist[0]
+    met = tried = 0
+    gains, fixed_fail = [], 0
+    for i in range(24):
+        sw = S.sweep(90_000 + i)
+        for t in (1e-4, 1e-6, 1e-8):
+            if S.label(sw, t) is None:
+                continue
+            n, P, fb = sel.select(sw["omega"], sw["half"], sw["amin"], sw["amax"], sw["lmax"], t)
+            mol, _, _ = S.sweep_molecule(90_000 + i)
+            rng = np.random.Generator(np.random.Philox(90_000 + i + 7))
+            idx = torch.as_tensor(rng.integers(0, mol.nbf, size=(96, 4)).astype(np.int32), device="cuda")
+            ref = S._entries(mol, S.N_REF, S.P_REF, idx)
+            err = float(np.linalg.norm(S._entries(mol, n, P, idx) - ref) / np.linalg.norm(ref))
+            err_fixed = float(np.linalg.norm(S._entries(mol, 32, 48, idx) - ref) / np.linalg.norm(ref))
+            tried += 1
+            met += err <= t
+            if err_fixed <= t:
+                gains.append((32 ** 3) / (n ** 3))
+            else:
+                fixed_fail += 1
+    print(f"selector: met {met}/{tried}; fixed (32,48) failed {fixed_fail}/{tried}; "
+          f"mean cost gain where both meet the target {np.mean(gains):.2f}x")
+    assert met >= 0.9 * tried
+    assert np.mean(gains) > 1.0
+    # checkpoint round trip
+    p = str(tmp_path / "sel.npz")
+    sel.save(p, meta={"sweeps": len(train)})
+    sel2 = S.Selector.load(p)
+    assert np.array_equal(sel.predict_raw(X[:50]), sel2.predict_raw(X[:50]))
