@@ -69,13 +69,51 @@ __global__ void k_hadamard_pairs(int n, int P, int64_t nrows, const int64_t* pai
     out[e] = pref * hadamard_entry(rr[e], cc[e], n, P, nrows, pair_row, row_c, S, T, w);
 }
 
+// Few entries: one warp per entry, the lanes share the quadrature nodes (p = lane, lane + 32, ...)
+// and their partial node sums are added by a warp reduction.
+__global__ void k_hadamard_pairs_warp(int n, int P, int64_t nrows, const int64_t* __restrict__ pair_row,
+                                      const double* __restrict__ row_c, const double* __restrict__ S,
+                                      const double* __restrict__ T, const double* __restrict__ w, double pref,
+                                      const int64_t* rr, const int64_t* cc, int64_t count, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (e >= count) return;
+  const int64_t r = rr[e], c = cc[e];
+  const int64_t j0 = pair_row[r], j1 = pair_row[r + 1], k0 = pair_row[c], k1 = pair_row[c + 1];
+  double s = 0.0;
+  for (int p = lane; p < P; p += 32) {
+    double acc = 0.0;
+    for (int64_t j = j0; j < j1; ++j)
+      for (int64_t k = k0; k < k1; ++k) {
+        double prod = row_c[j] * row_c[k];
+        for (int d = 0; d < 3; ++d) {
+          const double* tj = T + (((size_t)d * P + p) * nrows + j) * n;
+          const double* sk = S + ((size_t)d * nrows + k) * n;
+          double g = 0.0;
+          for (int b = 0; b < n; ++b) g += tj[b] * sk[b];
+          prod *= g;
+        }
+        acc += prod;
+      }
+    s += w[p] * acc;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[e] = pref * s;
+}
+
 void launch_hadamard_pairs(const PairTable& t, int n, int P, const double* d_S, const double* d_T,
                            const double* d_w, double pref, const int64_t* d_r, const int64_t* d_c, int64_t count,
                            double* d_out, cudaStream_t st) {
   if (count <= 0) return;
+  count_launch();
+  if (count < 152 * 128) {  // too few entries to fill the GPU one thread each
+    const int64_t threads = count * 32;
+    k_hadamard_pairs_warp<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, P, t.nrows, t.pair_row, t.row_c, d_S,
+                                                                            d_T, d_w, pref, d_r, d_c, count, d_out);
+    return;
+  }
   int blocks = (int)((count + 127) / 128);
   if (blocks > 152 * 32) blocks = 152 * 32;
-  count_launch();
   k_hadamard_pairs<<<blocks, 128, 0, st>>>(n, P, t.nrows, t.pair_row, t.row_c, d_S, d_T, d_w, pref, d_r, d_c, count,
                                           d_out);
 }

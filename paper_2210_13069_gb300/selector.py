@@ -9,7 +9,8 @@ entries of B computed by the library at each (n, P) against the same entries at 
 reference order.  Out of the trained range, or if asked, the conservative fixed (32, 48) is
 used instead.
 
-Every number here comes from the CUDA library; nothing calls the CPU oracle.
+Every number here comes from the CUDA library (Algorithm 1 entries); nothing calls the CPU
+oracle.
 """
 from __future__ import annotations
 
@@ -93,7 +94,7 @@ def _entries(mol, n: int, P: int, idx_dev) -> np.ndarray:
     import torch
     pl = lrtei.Plan(mol, "fp64", n=n, P=P)
     out = torch.empty(idx_dev.shape[0], dtype=torch.float64, device="cuda")
-    lrtei.lrtei_entries_noalloc(pl.plan, idx_dev, idx_dev.shape[0], out)
+    lrtei.lrtei_entries(pl.plan, idx_dev, idx_dev.shape[0], out)
     res = out.cpu().numpy()
     pl.close()
     return res

@@ -66,15 +66,15 @@ def test_selector_meets_target_and_gains_over_fixed(lib, tmp_path):
     chosen one is cheaper on average (cost ~ n^3 per J-build)."""
     import torch
     from paper_2210_13069_gb300 import selector as S
-    train = [S.sweep(10_000 + i) for i in range(260)]
+    train = [S.sweep(10_000 + i) for i in range(160)]
     X, Y = S.dataset(train)
-    assert len(X) > 600
+    assert len(X) > 400
     sel = S.Selector(64, seed=11)
     hist = sel.train(X, Y, epochs=250, batch=256, lr=2e-3)
     assert hist[-1] < hist[0]
     met = tried = 0
     gains, fixed_fail = [], 0
-    for i in range(24):
+    for i in range(16):
         sw = S.sweep(90_000 + i)
         for t in (1e-4, 1e-6, 1e-8):
             if S.label(sw, t) is None:
