@@ -107,7 +107,10 @@ lrtei_status lrtei_plan_status(lrtei_plan* plan);
 
 /* ---- full tensor (Theorem 1; eq. tensors) ----------------------------------------------
  * Writes all N_b^2 x N_b^2 entries of B, FP64, row-major with leading dimension ld >= N_b^2,
- * into the caller's device buffer d_B.  `form` selects the Hadamard or the factored form. */
+ * into the caller's buffer d_B: device memory, or page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister), which the final expansion kernel then writes directly across the
+ * host link.  Pageable host memory returns LRTEI_ERR_ARG.  `form` selects the Hadamard or the
+ * factored form. */
 lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, int64_t ld, void* stream);
 
 /* Rows [row_begin, row_end) of the unique-pair matrix B_u (rows and columns are unique pairs

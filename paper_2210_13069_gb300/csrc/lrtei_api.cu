@@ -781,6 +781,21 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
   const int nbf = plan->basis.nbf;
   const int64_t nb2 = (int64_t)nbf * nbf, npair = plan->t.npair;
   if (ld < nb2) { set_error("ld %lld < N_b^2 = %lld", (long long)ld, (long long)nb2); return LRTEI_ERR_ARG; }
+  // The output may be device memory or page-locked host memory; in the latter case the
+  // expansion kernel stores B through the buffer's device alias, so the device-to-host
+  // transfer is the kernel's own write stream (no staging copy of B in device memory).
+  {
+    cudaPointerAttributes pa{};
+    cudaError_t e = cudaPointerGetAttributes(&pa, d_B);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(B)");
+    if (pa.type == cudaMemoryTypeHost) {
+      if (!pa.devicePointer) { set_error("pinned host B is not mapped into the device address space"); return LRTEI_ERR_ARG; }
+      d_B = static_cast<double*>(pa.devicePointer);
+    } else if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) {
+      set_error("B must be device memory or page-locked (pinned) host memory");
+      return LRTEI_ERR_ARG;
+    }
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int f = choose_form(plan, form);
   plan->last_form = f;

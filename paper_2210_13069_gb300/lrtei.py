@@ -315,10 +315,13 @@ class Plan:
             pass
 
     def assemble_B(self, form: str = "auto", out=None, stream=None):
+        """B into `out`: a CUDA tensor, or a pinned CPU tensor (written directly by the device)."""
         torch = self._torch
         nb2 = self.nbf * self.nbf
         if out is None:
             out = torch.empty((nb2, nb2), dtype=torch.float64, device="cuda")
+        elif not out.is_cuda and not out.is_pinned():
+            raise ValueError("assemble_B: a host output must be pinned (page-locked) memory")
         lrtei_assemble_B(self.plan, FORMS[form], out, out.stride(0), stream)
         return out
 

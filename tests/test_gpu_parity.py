@@ -273,8 +273,9 @@ def test_split_f16_full_size_180(lib):
 
 @pytest.mark.parametrize("cfg", ["0", "1"])
 def test_split_f16_each_tile_config(lib, cfg, monkeypatch):
-    """Every kernel configuration the tuner may pick (64- and 32-deep K stages, 128x64 and
-    128x32 tiles) gives the same accuracy on B and J."""
+    """Every kernel configuration the tuner may pick (64- and 32-deep K stages; 128x128 tiles
+    for B, 128x64 and 128x32 tiles for J-builds of 40 and 7 densities) gives the same accuracy
+    on B and J; the 45-function instance leaves ragged tails in every tile shape."""
     import torch
     monkeypatch.setenv("LRTEI_TC_CONFIG", cfg)
     m = mol_ragged()
@@ -285,6 +286,30 @@ def test_split_f16_each_tile_config(lib, cfg, monkeypatch):
     pl.status()
     assert rel_fro(B, ref) <= 1e-7
     assert np.array_equal(B, B.T)
-    D = synth.random_densities(13, m.nbf, 40)
-    J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
-    assert rel_fro(J, o.jbuild_factored(D)) <= 1e-7
+    for R in (40, 7):
+        D = synth.random_densities(13, m.nbf, R)
+        J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+        assert rel_fro(J, o.jbuild_factored(D)) <= 1e-7, R
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_f16"])
+def test_assemble_B_into_pinned_host_memory(lib, precision):
+    """B written by the device straight into pinned host memory equals B in device memory, bit
+    for bit; pageable host memory is refused before any launch."""
+    import torch
+    m = mol_ragged()
+    pl = lib.Plan(m, precision)
+    Bd = pl.assemble_B().cpu()
+    nb2 = m.nbf * m.nbf
+    Bh = torch.full((nb2, nb2), float("nan"), dtype=torch.float64, pin_memory=True)
+    pl.assemble_B(out=Bh)
+    torch.cuda.synchronize()
+    pl.status()
+    assert torch.equal(Bd, Bh)
+    pageable = torch.empty((nb2, nb2), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        pl.assemble_B(out=pageable)
+    with pytest.raises(lib.LrteiError) as ei:
+        lib.lrtei_assemble_B(pl.plan, 0, pageable, nb2)
+    assert ei.value.status == 1
+    pl.close()
