@@ -35,7 +35,6 @@ METRIC = "LR-TEI entries/s & J-builds/s at ≤1e-7 rel err, mixed vs FP64 same G
 UNIT = "entries/s"
 WORKLOAD = ("nb180_spd: 12 atoms in a 12 bohr cube, 3s+2p+1d Cartesian shells x 3 primitives (N_b=180), "
             "exponents log-uniform [0.05, 2e3], omega=0.4, n=24, P=32; full 32400x32400 FP64 B per step")
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured figure in MEASURED_PEAKS.json)
 
 
 def parse_args():
@@ -236,6 +235,8 @@ def run_ours(args, world, rank, local):
     n3 = mol.n ** 3
     stream = torch.cuda.current_stream()
 
+    # CUDA-core FMA peaks of this device, measured (the FP64/FP32 roofline denominators)
+    fma_peaks = {"fp64_tflops": lrtei.lrtei_measure_fma_peak(True), "fp32_tflops": lrtei.lrtei_measure_fma_peak(False)}
     plan = lrtei.Plan(mol, args.precision)
     B = torch.empty((nb2, nb2), dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
@@ -285,28 +286,28 @@ def run_ours(args, world, rank, local):
         kname, src = "gemm_fp32", "paper_2210_13069_gb300/csrc/k_gemm.cu"
         tot_ms, cnt = prof["gemm_fp32"]
         flops_step = 2.0 * npair * npair * n3
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak = fma_peaks["fp32_tflops"]
         unit, bound, k_slices = "TFLOP/s", "alu", 1
     elif form_used == 1:
         kname, src = "hadamard", "paper_2210_13069_gb300/csrc/k_hadamard.cu"
         tot_ms, cnt = prof["hadamard"]
         Ibar2 = (lrtei.lrtei_plan_info_get(plan.plan)["nrows"] / npair) ** 2
         flops_step = npair * npair * mol.P * Ibar2 * (6 * mol.n + 3)
-        peak, unit, bound, k_slices = FP64_PEAK_TFLOPS, "TFLOP/s", "alu", 1
+        peak, unit, bound, k_slices = fma_peaks["fp64_tflops"], "TFLOP/s", "alu", 1
     else:
         kname, src = "gemm_fp64", "paper_2210_13069_gb300/csrc/k_gemm.cu"
         tot_ms, cnt = prof["gemm_fp64"]
         flops_step = 2.0 * npair * npair * n3
-        peak, unit, bound, k_slices = FP64_PEAK_TFLOPS, "TFLOP/s", "alu", 1
+        peak, unit, bound, k_slices = fma_peaks["fp64_tflops"], "TFLOP/s", "alu", 1
     roofline = None
     if cnt > 0 and tot_ms > 0:
         per_launch_flops = flops_step * args.steps / cnt
         avg_ms = tot_ms / cnt
         achieved = per_launch_flops / (avg_ms / 1e3) / 1e12
-        traffic = profiled_traffic(kname, "nb180_spd", src)
+        traffic = profiled_traffic(kname, "nb180_spd", src) if args.natoms == 12 else None
         roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind if bound == "tensor" else
-                    "nominal FP64/FP32 rate (not in MEASURED_PEAKS.json)", "launches_per_step": cnt / args.steps,
+                    "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind + " (bf16_tflops_sustained)" if
+                    bound == "tensor" else "measured (lrtei_measure_fma_peak)", "launches_per_step": cnt / args.steps,
                     "avg_launch_ms": avg_ms, "share_of_step": tot_ms / (ms_local * args.steps),
                     "split_products": k_slices,
                     "issued_frac": achieved * k_slices / peak}
@@ -382,13 +383,24 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        lrtei.lrtei_profile_reset()
+        lrtei.lrtei_profile_enable(True)
         f0.record(stream)
         p64.assemble_B(args.form, out=B)
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1)
+        g_ms, g_cnt = lrtei.lrtei_profile_get("gemm_fp64")
+        lrtei.lrtei_profile_enable(False)
+        lrtei.lrtei_profile_reset()
         fp64 = {"entries_per_s": world * entries_per_step / (max_over_ranks(ms64, world, device="cuda") / 1e3),
                 "ms_per_step": ms64}
+        if g_cnt > 0 and g_ms > 0:
+            # B_u = G F_u^T on the CUDA cores: 2 npair^2 n^3 flops per step
+            ach = 2.0 * npair * npair * n3 / (g_ms / 1e3) / 1e12
+            fp64["roofline"] = {"bound": "alu", "kernel": "gemm_fp64", "achieved": ach, "peak": fma_peaks["fp64_tflops"],
+                                "unit": "TFLOP/s", "frac": ach / fma_peaks["fp64_tflops"],
+                                "peak_kind": "measured (lrtei_measure_fma_peak)", "share_of_step": g_ms / ms64}
         if not args.no_jbuild:
             R = 32
             D = torch.as_tensor(synth.random_densities(4242, nbf, R), device="cuda")
@@ -430,7 +442,7 @@ def run_ours(args, world, rank, local):
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
             "jbuilds": jb, "fp64_same_gpu": fp64, "batched": batched, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -188,6 +188,14 @@ lrtei_status lrtei_profile_enable(int on);
 lrtei_status lrtei_profile_get(const char* kernel, double* total_ms, int64_t* launches);
 void lrtei_profile_reset(void);
 
+/* ---- CUDA-core FMA peak (measurement infrastructure; no counterpart in the paper) -------
+ * Runs a throughput-bound FMA kernel (FP64 if fp64 != 0, else FP32) on all SMs of the current
+ * device on `stream`, synchronises it, and writes the best of two timed launches in TFLOP/s
+ * (2 flops per FMA) to *tflops (host).  Used as the roofline denominator of the FP64/FP32
+ * CUDA-core kernels.  Allocates a small output buffer stream-ordered; LRTEI_ERR_CUDA on a
+ * device error, LRTEI_ERR_ARG if tflops is NULL. */
+lrtei_status lrtei_measure_fma_peak(int fp64, double* tflops, void* stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* lrtei_last_error(void);
 /* Library version string. */

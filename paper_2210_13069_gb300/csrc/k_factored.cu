@@ -52,7 +52,7 @@ template void launch_build_F<float>(const PairTable&, int, const double*, int64_
                                     cudaStream_t);
 
 // K(a, b) with a = (a1 n + a2) n + a3, b likewise; one thread per entry.
-__global__ void k_build_K(int n, int P, const double* __restrict__ C, const double* __restrict__ w,
+__global__ void k_build_K(int n, int P, const double* __restrict__ C, const double* __restrict__ w, double scale,
                           double* __restrict__ K) {
   const int n3 = n * n * n;
   const int64_t total = (int64_t)n3 * n3;
@@ -68,16 +68,16 @@ __global__ void k_build_K(int n, int P, const double* __restrict__ C, const doub
       const double* cz = C + ((size_t)2 * P + p) * nn;
       acc += w[p] * cx[a1 * n + b1] * cy[a2 * n + b2] * cz[a3 * n + b3];
     }
-    K[t] = acc;
+    K[t] = scale * acc;
   }
 }
 
-void launch_build_K(int n, int P, const double* d_C, const double* d_w, double* d_K, cudaStream_t st) {
+void launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K, cudaStream_t st) {
   const int64_t n3 = (int64_t)n * n * n;
   int64_t blocks = (n3 * n3 + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   count_launch();
-  k_build_K<<<(unsigned)blocks, 256, 0, st>>>(n, P, d_C, d_w, d_K);
+  k_build_K<<<(unsigned)blocks, 256, 0, st>>>(n, P, d_C, d_w, scale, d_K);
 }
 
 // Mode product on a tensor viewed as (I, n, Kd): out[i][a][k] = sum_m C[a][m] in[i][m][k].

@@ -14,13 +14,16 @@
 // rest carries 2^-11 of the weight.  The representation error is about 2^-31 of the row
 // maxima; the dropped products (t1 t2, t2 t1, t2 t2) are below 2^-29 of them.
 //
-// Kernel organisation (one 128 x BN output tile per CTA, 18 warps):
-//   warp 0       TMA producer: 3 A slices + 4 B slices per 64-deep K step into a ring of
-//                shared-memory stages (128-byte swizzle), mbarrier transaction counts
+// Kernel organisation (one 128 x BN output tile per CTA, BN = 128 for wide outputs):
+//   warp 0       TMA producer: 3 A slices + 4 B slices per 64- or 32-deep K step into a ring
+//                of shared-memory stages (128- or 64-byte swizzle), mbarrier transaction counts
 //   warp 1       TMEM allocation (512 columns) and the single MMA-issuing thread:
 //                6 tcgen05.mma (M=128, N=BN, K=16) per 16-deep k step into two accumulators,
-//                double-buffered across K chunks
-//   warps 2..17  epilogue: tcgen05.ld of each finished chunk, running sums, staged FP64 store
+//                double-buffered across K chunks, grouped by A slice (collector reuse)
+//   warps 2..    epilogue (16 warps, 8 for BN = 128): tcgen05.ld of each finished chunk,
+//                running sums, staged FP64 store
+// A 128 x 64 MMA is bound by its operand reads from shared memory (2/3 of the tensor rate
+// measured); from N = 128 on the pipe runs at its full rate.
 // Every mbarrier wait is bounded: on expiry the CTA raises the device status word, stops
 // issuing work, waits (bounded) for what it issued, frees TMEM and exits.
 #include <cuda.h>
@@ -48,7 +51,8 @@ constexpr int NA = 3;        // A slices: s0, t1, t2'
 constexpr int NB = 4;        // B slices: s0, t1, t1', t2'
 // Epilogue warps: 4 per TMEM lane quadrant for tiles up to 64 columns; 2 per quadrant for
 // 128-column tiles, whose running sums (two words per element, 128 per thread) need the larger
-// per-thread register share of a 10-warp block.
+// per-thread register share of a 10-warp block (measured slightly faster than 16 warps with
+// 64 sums each).
 template <int BN>
 __host__ __device__ constexpr int epi_warps() { return BN >= 128 ? 8 : 16; }
 template <int BN>
@@ -220,10 +224,41 @@ __device__ __forceinline__ double pow2(int k) {  // 2^k, exponent clamped to the
   return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
-// T0 + T12 / 2^11 of a staged tile element (T12 alone for plain BF16).
+// (T0 + T12 / 2^11) 2^k in integer arithmetic (this device's FP64 rate would make an FP64
+// epilogue a visible part of the GEMM): X = T0 2^20 + round(T12 2^9) is an integer below 2^53
+// (|T0| < 2^31; |T12| < 2^34 for K <= 32768), so X 2^(k-20) is exact in FP64 and is built from
+// its bits.  Rounding T12 to 2^-9 moves the result by at most 2^-21 of a unit of T0, far below
+// the 2^-31 representation error of the operands.  Results below the normal range flush to 0.
+__device__ __forceinline__ double combine_pow2(int t0, float t12, int k) {
+  const uint32_t fb = __float_as_uint(t12);
+  const int fe = (int)((fb >> 23) & 0xFFu);
+  int64_t q = 0;
+  if (fe != 0) {  // zero or subnormal T12 is below the 2^-9 resolution
+    const int64_t m = (int64_t)((fb & 0x7FFFFFu) | 0x800000u);
+    const int sh = fe - 127 - 23 + 9;  // T12 2^9 = m 2^sh
+    if (sh >= 0)
+      q = m << min(sh, 28);  // q < 2^52 (|T12| < 2^43)
+    else if (sh > -26)
+      q = (m + (1LL << (-sh - 1))) >> (-sh);
+    if (fb >> 31) q = -q;
+  }
+  const int64_t X = ((int64_t)t0 << 20) + q;
+  if (X == 0) return 0.0;
+  const uint64_t a = (uint64_t)(X < 0 ? -X : X);
+  const int lz = __clzll((long long)a);    // a < 2^53: lz >= 11
+  const uint64_t mant = a << (lz - 11);    // leading one at bit 52
+  const int E = 1023 + (63 - lz) + k - 20;  // X 2^(k-20) = 1.f 2^(E-1023)
+  if (E <= 0) return 0.0;
+  const uint64_t bits = ((uint64_t)(X < 0) << 63) | ((uint64_t)min(E, 2046) << 52) | (mant & ((1ULL << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+// Output element of a staged tile: scale 2^k (T0 + T12 / 2^11), or scale 2^k T12 for plain BF16.
 template <bool PLAIN>
-__device__ __forceinline__ double tile_value(const int* st0, const float* st12, int i) {
-  return PLAIN ? (double)st12[i] : (double)st0[i] + (double)st12[i] * (1.0 / 2048.0);
+__device__ __forceinline__ double tile_value(const int* st0, const float* st12, int i, int k, double scale) {
+  if constexpr (PLAIN) return scale * pow2(k) * (double)st12[i];
+  const double v = combine_pow2(st0[i], st12[i], k);
+  return scale == 1.0 ? v : scale * v;
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -403,7 +438,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       }
     }
   } else {
-    // ---------------------------------------------------------------- epilogue warps 2..17
+    // ---------------------------------------------------------------- epilogue warps
     const int ew = warp - 2;
     const int quad = warp & 3;             // TMEM lane quadrant this warp may access
     const int col0 = (ew >> 2) * QC;       // first column of this thread
@@ -420,26 +455,27 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       const int buf = c & 1;
       // one lane waits, the warp reconverges before the .sync.aligned TMEM loads
       int got = 1;
-      if (lane == 0) got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, abort_flag, p.status, 256) ? 1 : 0;
+      if (lane == 0) got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, abort_flag, p.status, 128) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) { ok = false; break; }
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 2 * BN + col0);
+      // both accumulators' loads of an 8-column group are in flight together (one wait per group)
 #pragma unroll
       for (int j0 = 0; j0 < QC; j0 += 8) {
-        uint32_t r[8];
+        uint32_t r[8], q[8];
         tmem_ld8(tbase + j0, r);
+        if constexpr (!PLAIN) tmem_ld8(tbase + BN + j0, q);
         tmem_wait_ld();
         if constexpr (PLAIN) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) T12[j0 + j] += __uint_as_float(r[j]);
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
-          tmem_ld8(tbase + BN + j0, r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) T12[j0 + j] += __uint_as_float(r[j]);
+          for (int j = 0; j < 8; ++j) {
+            T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
+            T12[j0 + j] += __uint_as_float(q[j]);
+          }
         }
       }
       tc_fence_before();
@@ -478,7 +514,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           const int r = idx / BN, c = idx % BN;
           const int64_t gm = m0 + r, gn = n0 + c;
           if (gm < p.M && gn < p.N && (!diag || gm <= gn))
-            Cs[gm * p.ldc + gn] = p.scale * pow2(sea[r] + seb[c] - 16) * tile_value<PLAIN>(st0, st12, r * LDS + c);
+            Cs[gm * p.ldc + gn] = tile_value<PLAIN>(st0, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
         }
       }
       if (p.transpose_out || p.symmetric) {  // C^T: consecutive threads along a column of C
@@ -486,7 +522,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           const int c = idx / BM, r = idx % BM;
           const int64_t gm = m0 + r, gn = n0 + c;
           if (gm < p.M && gn < p.N && (!diag || gm < gn))
-            Cs[gn * p.ldc + gm] = p.scale * pow2(sea[r] + seb[c] - 16) * tile_value<PLAIN>(st0, st12, r * LDS + c);
+            Cs[gn * p.ldc + gm] = tile_value<PLAIN>(st0, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
         }
       }
     }

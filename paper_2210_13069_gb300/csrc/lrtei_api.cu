@@ -490,8 +490,10 @@ struct Scratch {
   }
 };
 
-// Dense K = sum_p w_p A_x^p (x) A_y^p (x) A_z^p as slices; the fourth plane only when K is the
-// B operand (G = F_u K); the J-build uses K as the A operand.
+// Dense K = (omega / sqrt(pi)) sum_p w_p A_x^p (x) A_y^p (x) A_z^p as slices: the prefactor of
+// eq. approx33 is carried by K, so that every tensor-core GEMM runs with scale 1 and its
+// epilogue needs no FP64 multiply.  The fourth plane only when K is the B operand (G = F_u K);
+// the J-build uses K as the A operand.
 lrtei_status ensure_Ksp(lrtei_plan* pl, cudaStream_t st, bool need_s1h) {
   if (pl->have_Ksp && (!need_s1h || pl->Ksp.plain || pl->Ksp.s1h)) return LRTEI_OK;
   if (pl->have_Ksp) {
@@ -502,7 +504,7 @@ lrtei_status ensure_Ksp(lrtei_plan* pl, cudaStream_t st, bool need_s1h) {
   Scratch sc(st);
   double* K;
   LRTEI_TRY(sc.get(&K, (size_t)n3 * n3));
-  launch_build_K(pl->n, pl->P, pl->d_C, pl->d_w, K, st);
+  launch_build_K(pl->n, pl->P, pl->d_C, pl->d_w, pl->omega / sqrt(kPi), K, st);
   LRTEI_TRY(alloc_split(pl, pl->Ksp, n3, n3, need_s1h));
   {
     ProfScope ps("split", st);
@@ -561,9 +563,8 @@ int splits_for(int64_t M, int64_t K) {
   return (int)s;
 }
 
-// Rows [r0, r1) of B_u through the tensor-core GEMMs (split precision), prefactor included.
+// Rows [r0, r1) of B_u through the tensor-core GEMMs (split precision); the prefactor is in K.
 lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int64_t ld, cudaStream_t st) {
-  const double pref = pl->omega / sqrt(3.14159265358979323846);
   const int64_t n3 = (int64_t)pl->n * pl->n * pl->n, npair = pl->t.npair, nr = r1 - r0;
   LRTEI_TRY(ensure_Fsp(pl, st, true));
   LRTEI_TRY(ensure_Ksp(pl, st, true));
@@ -585,7 +586,7 @@ lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int
     launch_split_rows(G, nr, n3, n3, Gs, false, nslices(pl), st);
   }
   const bool sym = (r0 == 0 && r1 == npair && ld == npair);
-  return tc_gemm(Gs, pl->Fsp, nr, npair, pref, out, ld, false, sym, 1, nullptr, pl->d_status, st);
+  return tc_gemm(Gs, pl->Fsp, nr, npair, 1.0, out, ld, false, sym, 1, nullptr, pl->d_status, st);
 }
 
 int choose_form(const lrtei_plan* pl, lrtei_form form) {
@@ -858,8 +859,7 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
 static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st) {
   const int nbf = plan->basis.nbf, n = plan->n;
   const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;
-  const double pref = plan->omega / sqrt(kPi);
-  LRTEI_TRY(ensure_jbuild_operands(plan, st));
+  LRTEI_TRY(ensure_jbuild_operands(plan, st));  // K carries the prefactor omega / sqrt(pi)
   Scratch sc(st);
   double *Du, *DuT, *XT, *YT, *Ju, *part;
   LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
@@ -894,7 +894,7 @@ static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double
   }
   // J_u = F Y : npair x R
   LRTEI_TRY(tc_gemm(plan->Fsp, Ysp, npair, R, 1.0, Ju, R, false, false, s3, part, plan->d_status, st));
-  launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+  launch_unpack_J(nbf, R, Ju, 1.0, d_J, st);
   return finish_launch("jbuild (tensor cores)");
 }
 

@@ -87,6 +87,7 @@ def load():
         "lrtei_profile_enable": (S, [ctypes.c_int]),
         "lrtei_profile_get": (S, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "lrtei_profile_reset": (None, []),
+        "lrtei_measure_fma_peak": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]),
         "lrtei_last_error": (ctypes.c_char_p, []),
         "lrtei_version": (ctypes.c_char_p, []),
     }
@@ -216,6 +217,13 @@ def lrtei_profile_enable(on: bool):
 
 def lrtei_profile_reset():
     load().lrtei_profile_reset()
+
+
+def lrtei_measure_fma_peak(fp64: bool, stream=None) -> float:
+    """Measured CUDA-core FMA rate in TFLOP/s (FP64 or FP32), all SMs of the current device."""
+    tf = ctypes.c_double(0.0)
+    _check(load().lrtei_measure_fma_peak(1 if fp64 else 0, ctypes.byref(tf), _stream(stream)))
+    return tf.value
 
 
 def lrtei_profile_get(kernel: str):
