@@ -43,7 +43,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="split_f16", choices=["split_f16", "fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="split_f16", choices=["split_f16", "split_f16_8", "fp64", "fp32", "bf16"])
     ap.add_argument("--form", default="factored", choices=["auto", "hadamard", "factored"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-nb360", action="store_true")
     ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="oracle seconds per step of the reference arm (default: the run stays within ~2.5 min)")
@@ -281,9 +282,9 @@ def run_ours(args, world, rank, local):
     # ---- roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
     form_used = plan.info and lrtei.lrtei_plan_info_get(plan.plan)["last_form"]
-    if args.precision in ("split_f16", "bf16"):
+    if args.precision in ("split_f16", "split_f16_8", "bf16"):
         kname, src = "tc_gemm", "paper_2210_13069_gb300/csrc/k_tcgen05.cu"
-        k_slices = 6 if args.precision == "split_f16" else 1
+        k_slices = {"split_f16": 6, "split_f16_8": 8, "bf16": 1}[args.precision]
         tot_ms, cnt = prof["tc_gemm"]
         # algorithmic flops per step of the tensor-core GEMMs: G = F K (npair x n3 x n3) and the
         # upper-triangular tiles of B_u = G F^T (npair^2 n3), one product each
@@ -426,10 +427,60 @@ def run_ours(args, world, rank, local):
             fp64["speedup_jbuilds"] = jb["value"] / fp64["jbuilds_per_s"]
         p64.close()
 
+    # ---- the same step with the eight-product scheme (error about seven times smaller)
+    split8 = None
+    if args.precision == "split_f16" and not args.no_fp64:
+        p8 = lrtei.Plan(mol, "split_f16_8")
+        for _ in range(2):
+            p8.assemble_B(args.form, out=B)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(3):
+            p8.assemble_B(args.form, out=B)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        p8.status()
+        ms8 = h0.elapsed_time(h1) / 3
+        split8 = {"entries_per_s": whole_job_rate(entries_per_step, world, ms8, device="cuda"), "ms_per_step": ms8}
+        p8.close()
+
     # ---- batched J-builds: 64 molecules of uneven size, 16 densities each
     batched = None
-    if not args.no_batched and args.precision in ("split_f16", "bf16"):
+    if not args.no_batched and args.precision in ("split_f16", "split_f16_8", "bf16"):
         batched = run_batched(args, world)
+
+    # ---- the 360-function instance (24 atoms, omega = 0.33): full 129 600^2 B (134 GB) per step.
+    # Six products measured 1.06e-7 on sampled rows of it: it runs the eight-product scheme.
+    nb360 = None
+    if not args.no_nb360 and args.natoms == 12:
+        del B
+        torch.cuda.empty_cache()
+        m360 = synth.workload_spd_large()
+        e360 = float(m360.nbf) ** 4
+        prec360 = "split_f16_8" if args.precision == "split_f16" else args.precision
+        p360 = lrtei.Plan(m360, prec360)
+        B360 = torch.empty((m360.nbf ** 2, m360.nbf ** 2), dtype=torch.float64, device="cuda")
+        p360.assemble_B(args.form, out=B360)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        reps = 2
+        barrier(world)
+        g0.record(stream)
+        for _ in range(reps):
+            p360.assemble_B(args.form, out=B360)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        p360.status()
+        ms360 = g0.elapsed_time(g1) / reps
+        nb360 = {"workload": "nb360_spd: 24 atoms in a 15.1 bohr cube, same shells, omega=0.33, n=24, P=32",
+                 "entries_per_s": whole_job_rate(e360, world, ms360, device="cuda"), "ms_per_step": ms360,
+                 "steps": reps, "entries_per_step": e360, "precision": prec360}
+        p360.close()
+        del B360
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -437,7 +488,9 @@ def run_ours(args, world, rank, local):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        dtype = {"split_f16": "f16x3 (8+11+11-bit integer slices, fp32 acc)", "bf16": "bf16", "fp64": "f64", "fp32": "f32"}[
+        dtype = {"split_f16": "f16x3 (8+11+11-bit integer slices, fp32 acc)",
+                 "split_f16_8": "f16x3 (8+11+11-bit integer slices, 8 products, 3 fp32 accumulators)",
+                 "bf16": "bf16", "fp64": "f64", "fp32": "f32"}[
             args.precision]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -449,7 +502,7 @@ def run_ours(args, world, rank, local):
                        "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
-            "jbuilds": jb, "fp64_same_gpu": fp64, "batched": batched, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "jbuilds": jb, "fp64_same_gpu": fp64, "split_f16_8": split8, "batched": batched, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)

@@ -4,6 +4,8 @@
 // K is applied either densely (tensor-core path) or by three mode products per node (eq. ig1).
 // Also the symmetric expansion of the unique-pair matrix B_u into the full N_b^2 x N_b^2 B and
 // the density packing of the J-build (Section 5).
+#include <algorithm>
+
 #include "lrtei_internal.h"
 
 namespace lrtei {
@@ -72,11 +74,63 @@ __global__ void k_build_K(int n, int P, const double* __restrict__ C, const doub
   }
 }
 
+// The same K with one FMA per node and entry: block (a1, b1, part); thread (a3, b3) holds its P
+// values C_z^p(a3, b3) in registers; for each (a2, b2) the block shares r_p = scale w_p
+// C_x^p(a1, b1) C_y^p(a2, b2) through shared memory (kKGroup (a2, b2) at a time).  For fixed
+// (a2, b2) the block writes n-entry runs of consecutive columns.
+constexpr int kKGroup = 8;
+constexpr int kKThreads = 512;
+template <int PMAX>
+__global__ void __launch_bounds__(kKThreads) k_build_K_rows(int n, int P, int parts, const double* __restrict__ C,
+                                                            const double* __restrict__ w, double scale,
+                                                            double* __restrict__ K) {
+  __shared__ double r[kKGroup * PMAX];
+  const int nn = n * n;
+  const int64_t n3 = (int64_t)nn * n;
+  const int ab = blockIdx.x / parts, part = blockIdx.x % parts;
+  const int a1 = ab / n, b1 = ab % n;
+  const int e = part * kKThreads + threadIdx.x;  // (a3, b3) = (e / n, e % n)
+  const bool live = e < nn;
+  const int a3 = e / n, b3 = e % n;
+  double cz[PMAX];
+#pragma unroll
+  for (int p = 0; p < PMAX; ++p) cz[p] = (live && p < P) ? C[((size_t)2 * P + p) * nn + e] : 0.0;
+  for (int c0 = 0; c0 < nn; c0 += kKGroup) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kKGroup * P; i += blockDim.x) {
+      const int c = c0 + i / P, p = i % P;
+      r[(i / P) * PMAX + p] =
+          c < nn ? scale * w[p] * C[(size_t)p * nn + a1 * n + b1] * C[((size_t)P + p) * nn + c] : 0.0;
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int g = 0; g < kKGroup && c0 + g < nn; ++g) {
+      const int a2 = (c0 + g) / n, b2 = (c0 + g) % n;
+      double acc = 0.0;
+#pragma unroll
+      for (int p = 0; p < PMAX; ++p)
+        if (p < P) acc = fma(r[g * PMAX + p], cz[p], acc);
+      K[((int64_t)(a1 * n + a2) * n + a3) * n3 + ((int64_t)(b1 * n + b2) * n + b3)] = acc;
+    }
+  }
+}
+
 void launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K, cudaStream_t st) {
   const int64_t n3 = (int64_t)n * n * n;
+  const int nn = n * n;
+  count_launch();
+  if (P <= 48) {
+    const int parts = (nn + kKThreads - 1) / kKThreads;
+    const int threads = std::min(kKThreads, (nn + 31) / 32 * 32);
+    const unsigned blocks = (unsigned)(nn * parts);
+    if (P <= 32)
+      k_build_K_rows<32><<<blocks, threads, 0, st>>>(n, P, parts, d_C, d_w, scale, d_K);
+    else
+      k_build_K_rows<48><<<blocks, threads, 0, st>>>(n, P, parts, d_C, d_w, scale, d_K);
+    return;
+  }
   int64_t blocks = (n3 * n3 + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  count_launch();
   k_build_K<<<(unsigned)blocks, 256, 0, st>>>(n, P, d_C, d_w, scale, d_K);
 }
 

@@ -13,6 +13,10 @@
 // The leading term is exact whatever rounding the tensor core applies to its FP32 sums; the
 // rest carries 2^-11 of the weight.  The representation error is about 2^-31 of the row
 // maxima; the dropped products (t1 t2, t2 t1, t2 t2) are below 2^-29 of them.
+// The tensor core's FP32 accumulation truncates (measured against an emulation), so L12's
+// smaller terms are cut at the scale of its s0 t1 terms.  The eight-product variant (P8) keeps
+// t1 t2 and t2 t1 as well and splits L12 into L1 = s0 t1 + t1 s0 and L2 (the rest, in its own
+// accumulator): three accumulators per buffer, 128 x 64 tiles, C from T0 + (T1 + T2) / 2^11.
 //
 // Kernel organisation (one 128 x BN output tile per CTA, BN = 128 for wide outputs):
 //   warp 0       TMA producer: 3 A slices + 4 B slices per 64- or 32-deep K step into a ring
@@ -229,20 +233,26 @@ __device__ __forceinline__ double pow2(int k) {  // 2^k, exponent clamped to the
 // (|T0| < 2^31; |T12| < 2^34 for K <= 32768), so X 2^(k-20) is exact in FP64 and is built from
 // its bits.  Rounding T12 to 2^-9 moves the result by at most 2^-21 of a unit of T0, far below
 // the 2^-31 representation error of the operands.  Results below the normal range flush to 0.
-__device__ __forceinline__ double combine_pow2(int t0, float t12, int k) {
-  const uint32_t fb = __float_as_uint(t12);
+// round(f 2^9) as an integer, from the bits of the FP32 value f.
+__device__ __forceinline__ int64_t round_2p9(float f) {
+  const uint32_t fb = __float_as_uint(f);
   const int fe = (int)((fb >> 23) & 0xFFu);
   int64_t q = 0;
-  if (fe != 0) {  // zero or subnormal T12 is below the 2^-9 resolution
+  if (fe != 0) {  // zero or subnormal f is below the 2^-9 resolution
     const int64_t m = (int64_t)((fb & 0x7FFFFFu) | 0x800000u);
-    const int sh = fe - 127 - 23 + 9;  // T12 2^9 = m 2^sh
+    const int sh = fe - 127 - 23 + 9;  // f 2^9 = m 2^sh
     if (sh >= 0)
-      q = m << min(sh, 28);  // q < 2^52 (|T12| < 2^43)
+      q = m << min(sh, 27);  // q < 2^51 (|f| < 2^42)
     else if (sh > -26)
       q = (m + (1LL << (-sh - 1))) >> (-sh);
     if (fb >> 31) q = -q;
   }
-  const int64_t X = ((int64_t)t0 << 20) + q;
+  return q;
+}
+
+// t2: a second FP32 sum of the same weight as t12 (the three-accumulator scheme), else 0.
+__device__ __forceinline__ double combine_pow2(int t0, float t12, int k, float t2 = 0.f) {
+  const int64_t X = ((int64_t)t0 << 20) + round_2p9(t12) + round_2p9(t2);
   if (X == 0) return 0.0;
   const uint64_t a = (uint64_t)(X < 0 ? -X : X);
   const int lz = __clzll((long long)a);    // a < 2^53: lz >= 11
@@ -254,31 +264,36 @@ __device__ __forceinline__ double combine_pow2(int t0, float t12, int k) {
 }
 
 // Output element of a staged tile: scale 2^k (T0 + T12 / 2^11), or scale 2^k T12 for plain BF16.
-template <bool PLAIN>
-__device__ __forceinline__ double tile_value(const int* st0, const float* st12, int i, int k, double scale) {
+template <bool PLAIN, bool P8>
+__device__ __forceinline__ double tile_value(const int* st0, const float* st12, const float* st2, int i, int k,
+                                            double scale) {
   if constexpr (PLAIN) return scale * pow2(k) * (double)st12[i];
-  const double v = combine_pow2(st0[i], st12[i], k);
+  const double v = combine_pow2(st0[i], st12[i], k, P8 ? st2[i] : 0.f);
   return scale == 1.0 ? v : scale * v;
 }
 
 // ------------------------------------------------------------------ the kernel
 // PLAIN: one BF16 operand plane each, one product per k step, FP32 sums (no exactness).
-template <int BN, int BK, int STAGES, bool PLAIN>
+// P8: eight products per k step (the next-order terms t1 t2' / 2^11 and t2' t1 / 2^11 kept, with
+// a fourth A slice t1 / 2^11) into three accumulators.
+template <int BN, int BK, int STAGES, bool PLAIN, bool P8>
 __global__ void __launch_bounds__(block_threads<BN>(), 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
-              const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
-              const __grid_constant__ CUtensorMap tb1, const __grid_constant__ CUtensorMap tb1h,
-              const __grid_constant__ CUtensorMap tb2, const Params p) {
+              const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap ta1h,
+              const __grid_constant__ CUtensorMap tb0, const __grid_constant__ CUtensorMap tb1,
+              const __grid_constant__ CUtensorMap tb1h, const __grid_constant__ CUtensorMap tb2, const Params p) {
   constexpr uint32_t A_BYTES = BM * BK * 2;
   constexpr uint32_t B_BYTES = BN * BK * 2;
-  constexpr int NA_ = PLAIN ? 1 : NA, NB_ = PLAIN ? 1 : NB;
+  constexpr int NA_ = PLAIN ? 1 : (P8 ? NA + 1 : NA), NB_ = PLAIN ? 1 : NB;
   constexpr uint32_t STAGE_BYTES = NA_ * A_BYTES + NB_ * B_BYTES;
   constexpr int KSTEPS = KCHUNK / BK;  // pipeline stages per chunk
   constexpr int QC = BN / (epi_warps<BN>() / 4);  // columns per epilogue thread
+  constexpr int NACC = P8 ? 3 : 2;                 // accumulators per buffer: L0, L12 (L1, L2 if P8)
+  static_assert(2 * NACC * BN <= 512, "two buffers of the accumulators must fit in TMEM");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 8 + (BM + BN) * 4;
+  constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 4 * (P8 ? 3 : 2) + (BM + BN) * 4;
   constexpr uint32_t RING_BYTES = (STAGES * STAGE_BYTES > TILE_BYTES) ? STAGES * STAGE_BYTES : TILE_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ((RING_BYTES + 7) & ~7u));
   uint64_t* empty = full + STAGES;
@@ -375,6 +390,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           tma_load_2d(&tb1, sb + 1 * B_BYTES, &full[s], kx, (int)n0);
           tma_load_2d(&tb1h, sb + 2 * B_BYTES, &full[s], kx, (int)n0);
           tma_load_2d(&tb2, sb + 3 * B_BYTES, &full[s], kx, (int)n0);
+          if constexpr (P8) tma_load_2d(&ta1h, st + 3 * A_BYTES, &full[s], kx, (int)m0);
         }
         issued = it + 1;
       }
@@ -397,8 +413,9 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
         const int buf = c & 1;
         if (!mbar_wait(&acce[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d0 = tmem_base + (uint32_t)(buf * 2 * BN);
+        const uint32_t d0 = tmem_base + (uint32_t)(buf * NACC * BN);
         const uint32_t d1 = d0 + BN;
+        const uint32_t d2 = P8 ? d0 + 2 * BN : d1;
         for (int step = 0; step < KSTEPS; ++step) {
           const int it = c * KSTEPS + step;
           const int s = it % STAGES;
@@ -406,7 +423,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           tc_fence_after();
           const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
           const uint64_t a0 = smem_desc<BK>(base), a1 = smem_desc<BK>(base + A_BYTES),
-                         a2 = smem_desc<BK>(base + 2 * A_BYTES);
+                         a2 = smem_desc<BK>(base + 2 * A_BYTES), a1h = smem_desc<BK>(base + 3 * A_BYTES);
           const uint32_t bb = base + NA_ * A_BYTES;
           const uint64_t b0 = smem_desc<BK>(bb), b1 = smem_desc<BK>(bb + B_BYTES), b1h = smem_desc<BK>(bb + 2 * B_BYTES),
                          b2 = smem_desc<BK>(bb + 3 * B_BYTES);
@@ -418,12 +435,20 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
               mma_bf16(d0, a0 + o, b0 + o, idesc, first);
             } else {
               // grouped by A slice so that each is read from shared memory once per k step
+              // P8: L1 = s0 t1 + t1 s0 in d1, the smaller terms in their own accumulator d2, so
+              // that the tensor core's truncating FP32 accumulation cuts them at their own scale
               mma_bf16_a<ACol::fill>(d0, a0 + o, b0 + o, idesc, first);
               mma_bf16_a<ACol::use>(d1, a0 + o, b1 + o, idesc, first);
-              mma_bf16_a<ACol::lastuse>(d1, a0 + o, b2 + o, idesc, 1u);
+              mma_bf16_a<ACol::lastuse>(d2, a0 + o, b2 + o, idesc, P8 ? first : 1u);
               mma_bf16_a<ACol::fill>(d1, a1 + o, b0 + o, idesc, 1u);
-              mma_bf16_a<ACol::lastuse>(d1, a1 + o, b1h + o, idesc, 1u);
-              mma_bf16(d1, a2 + o, b0 + o, idesc, 1u);
+              mma_bf16_a<ACol::lastuse>(d2, a1 + o, b1h + o, idesc, 1u);
+              if constexpr (P8) {
+                mma_bf16_a<ACol::fill>(d2, a2 + o, b0 + o, idesc, 1u);
+                mma_bf16_a<ACol::lastuse>(d2, a2 + o, b1h + o, idesc, 1u);  // t2' t1 / 2^11
+                mma_bf16(d2, a1h + o, b2 + o, idesc, 1u);                  // t1 / 2^11 t2'
+              } else {
+                mma_bf16(d1, a2 + o, b0 + o, idesc, 1u);
+              }
             }
           }
           mma_commit(&empty[s]);  // stage s may be refilled once these MMAs retire
@@ -445,10 +470,12 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     const int row = quad * 32 + lane;      // row inside the tile
     int T0[QC];
     float T12[QC];
+    float T2[P8 ? QC : 1];
 #pragma unroll
     for (int j = 0; j < QC; ++j) {
       T0[j] = 0;
       T12[j] = 0.f;
+      if constexpr (P8) T2[j] = 0.f;
     }
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
@@ -459,7 +486,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) { ok = false; break; }
       tc_fence_after();
-      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 2 * BN + col0);
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * NACC * BN + col0);
       // both accumulators' loads of an 8-column group are in flight together (one wait per group)
 #pragma unroll
       for (int j0 = 0; j0 < QC; j0 += 8) {
@@ -476,6 +503,12 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
             T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
             T12[j0 + j] += __uint_as_float(q[j]);
           }
+          if constexpr (P8) {
+            tmem_ld8(tbase + 2 * BN + j0, q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) T2[j0 + j] += __uint_as_float(q[j]);
+          }
         }
       }
       tc_fence_before();
@@ -489,7 +522,8 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     constexpr int LDS = BN + 1;  // padded row stride (words) against bank conflicts
     int* st0 = reinterpret_cast<int*>(smem);
     float* st12 = reinterpret_cast<float*>(st0 + BM * LDS);
-    int* sea = reinterpret_cast<int*>(st12 + BM * LDS);
+    float* st2 = st12 + BM * LDS;  // P8 only
+    int* sea = reinterpret_cast<int*>(st2 + (P8 ? BM * LDS : 0));
     int* seb = sea + BM;
     const bool good = ok && !*abort_flag;
     if (good) {
@@ -497,6 +531,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       for (int j = 0; j < QC; ++j) {
         st0[row * LDS + col0 + j] = T0[j];
         st12[row * LDS + col0 + j] = T12[j];
+        if constexpr (P8) st2[row * LDS + col0 + j] = T2[j];
       }
     }
     constexpr int NE = 32 * epi_warps<BN>();
@@ -514,7 +549,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           const int r = idx / BN, c = idx % BN;
           const int64_t gm = m0 + r, gn = n0 + c;
           if (gm < p.M && gn < p.N && (!diag || gm <= gn))
-            Cs[gm * p.ldc + gn] = tile_value<PLAIN>(st0, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
+            Cs[gm * p.ldc + gn] = tile_value<PLAIN, P8>(st0, st12, st2, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
         }
       }
       if (p.transpose_out || p.symmetric) {  // C^T: consecutive threads along a column of C
@@ -522,7 +557,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           const int c = idx / BM, r = idx % BM;
           const int64_t gm = m0 + r, gn = n0 + c;
           if (gm < p.M && gn < p.N && (!diag || gm < gn))
-            Cs[gn * p.ldc + gm] = tile_value<PLAIN>(st0, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
+            Cs[gn * p.ldc + gm] = tile_value<PLAIN, P8>(st0, st12, st2, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
         }
       }
     }
@@ -726,41 +761,46 @@ static bool encode_plane(CUtensorMap* m, const uint16_t* base, int64_t rows, int
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int BK, int STAGES, bool PLAIN>
+template <int BN, int BK, int STAGES, bool PLAIN, bool P8>
 static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits,
                               cudaStream_t st) {
-  CUtensorMap m[7];
+  CUtensorMap m[8];  // A: s0, s1, s2, s1h (eight-product scheme); B: s0, s1, s1h, s2
   bool ok;
   if (PLAIN) {
-    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, true, BK) && encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, true, BK);
-    m[1] = m[2] = m[0];
-    m[4] = m[5] = m[6] = m[3];
+    ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, true, BK) && encode_plane(&m[4], B.s0, B.rows, B.kpad, BN, true, BK);
+    m[1] = m[2] = m[3] = m[0];
+    m[5] = m[6] = m[7] = m[4];
   } else {
     ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, false, BK) &&
          encode_plane(&m[1], A.s1, A.rows, A.kpad, BM, false, BK) &&
          encode_plane(&m[2], A.s2, A.rows, A.kpad, BM, false, BK) &&
-         encode_plane(&m[3], B.s0, B.rows, B.kpad, BN, false, BK) &&
-         encode_plane(&m[4], B.s1, B.rows, B.kpad, BN, false, BK) &&
-         encode_plane(&m[5], B.s1h, B.rows, B.kpad, BN, false, BK) &&
-         encode_plane(&m[6], B.s2, B.rows, B.kpad, BN, false, BK);
+         encode_plane(&m[4], B.s0, B.rows, B.kpad, BN, false, BK) &&
+         encode_plane(&m[5], B.s1, B.rows, B.kpad, BN, false, BK) &&
+         encode_plane(&m[6], B.s1h, B.rows, B.kpad, BN, false, BK) &&
+         encode_plane(&m[7], B.s2, B.rows, B.kpad, BN, false, BK);
+    if (ok && P8) ok = encode_plane(&m[3], A.s1h, A.rows, A.kpad, BM, false, BK);
+    if (!P8) m[3] = m[0];
   }
   if (!ok) {
     set_error("cuTensorMapEncodeTiled failed (driver entry point unavailable or bad operand layout)");
     return LRTEI_ERR_CUDA;
   }
-  constexpr size_t stage = (size_t)(PLAIN ? 1 : NA) * BM * BK * 2 + (size_t)(PLAIN ? 1 : NB) * BN * BK * 2;
-  const size_t tile_bytes = (size_t)BM * (BN + 1) * 8 + (BM + BN) * 4;
+  constexpr size_t stage =
+      (size_t)(PLAIN ? 1 : (P8 ? NA + 1 : NA)) * BM * BK * 2 + (size_t)(PLAIN ? 1 : NB) * BN * BK * 2;
+  const size_t tile_bytes = (size_t)BM * (BN + 1) * 4 * (P8 ? 3 : 2) + (BM + BN) * 4;
   const size_t smem = std::max(STAGES * stage, tile_bytes) + 1024 + 256;
   static bool attr_set = false;  // once per instantiation (also keeps it out of stream capture)
   cudaError_t e = cudaSuccess;
   if (!attr_set) {
-    e = cudaFuncSetAttribute(k_tc_gemm<BN, BK, STAGES, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_tc_gemm<BN, BK, STAGES, PLAIN, P8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "tc_gemm smem attribute");
     attr_set = true;
   }
   dim3 grid((unsigned)p.ntiles, (unsigned)splits);
   count_launch();
-  k_tc_gemm<BN, BK, STAGES, PLAIN><<<grid, block_threads<BN>(), smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);
+  k_tc_gemm<BN, BK, STAGES, PLAIN, P8>
+      <<<grid, block_threads<BN>(), smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tc_gemm launch");
   return LRTEI_OK;
@@ -776,12 +816,13 @@ void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld,
     tc::k_plain_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.expo);
     return;
   }
+  uint16_t* s1h = (with_s1h || m.eight) ? m.s1h : nullptr;
   if (k <= 1024 * 16)
-    tc::k_split_rows_reg<16><<<(unsigned)rows, 1024, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2,
-                                                             with_s1h ? m.s1h : nullptr, m.expo, nslices);
+    tc::k_split_rows_reg<16><<<(unsigned)rows, 1024, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h,
+                                                             m.expo, nslices);
   else
-    tc::k_split_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2,
-                                                     with_s1h ? m.s1h : nullptr, m.expo, nslices);
+    tc::k_split_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h, m.expo,
+                                                     nslices);
 }
 
 void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,
@@ -808,6 +849,10 @@ struct Config {
   int bn, bk, stages;
 };
 static const Config kSplitCfg128[] = {{128, 64, 2}, {128, 32, 4}};
+// eight products, three accumulators (at most 64-column tiles: 2 x 3 x 64 TMEM columns), a
+// fourth A plane
+static const Config kSplit8Cfg64[] = {{64, 64, 2}, {64, 32, 4}};
+static const Config kSplit8Cfg32[] = {{32, 64, 2}, {32, 32, 5}};
 static const Config kSplitCfg64[] = {{64, 64, 2}, {64, 32, 5}};
 static const Config kSplitCfg32[] = {{32, 64, 3}, {32, 32, 6}};
 static const Config kPlainCfg64[] = {{64, 64, 6}, {64, 32, 8}};
@@ -815,16 +860,22 @@ static const Config kPlainCfg32[] = {{32, 64, 6}, {32, 32, 8}};
 
 static lrtei_status launch_cfg(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits, bool plain,
                                const Config& c, cudaStream_t st) {
-  if (plain) {
-    if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 6, true>(A, B, p, splits, st)
-                                      : launch_tc<64, 32, 8, true>(A, B, p, splits, st);
-    return c.bk == 64 ? launch_tc<32, 64, 6, true>(A, B, p, splits, st) : launch_tc<32, 32, 8, true>(A, B, p, splits, st);
+  if (A.eight) {
+    if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 2, false, true>(A, B, p, splits, st)
+                                      : launch_tc<64, 32, 4, false, true>(A, B, p, splits, st);
+    return c.bk == 64 ? launch_tc<32, 64, 2, false, true>(A, B, p, splits, st)
+                      : launch_tc<32, 32, 5, false, true>(A, B, p, splits, st);
   }
-  if (c.bn == 128) return c.bk == 64 ? launch_tc<128, 64, 2, false>(A, B, p, splits, st)
-                                     : launch_tc<128, 32, 4, false>(A, B, p, splits, st);
-  if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 2, false>(A, B, p, splits, st)
-                                    : launch_tc<64, 32, 5, false>(A, B, p, splits, st);
-  return c.bk == 64 ? launch_tc<32, 64, 3, false>(A, B, p, splits, st) : launch_tc<32, 32, 6, false>(A, B, p, splits, st);
+  if (plain) {
+    if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 6, true, false>(A, B, p, splits, st)
+                                      : launch_tc<64, 32, 8, true, false>(A, B, p, splits, st);
+    return c.bk == 64 ? launch_tc<32, 64, 6, true, false>(A, B, p, splits, st) : launch_tc<32, 32, 8, true, false>(A, B, p, splits, st);
+  }
+  if (c.bn == 128) return c.bk == 64 ? launch_tc<128, 64, 2, false, false>(A, B, p, splits, st)
+                                     : launch_tc<128, 32, 4, false, false>(A, B, p, splits, st);
+  if (c.bn == 64) return c.bk == 64 ? launch_tc<64, 64, 2, false, false>(A, B, p, splits, st)
+                                    : launch_tc<64, 32, 5, false, false>(A, B, p, splits, st);
+  return c.bk == 64 ? launch_tc<32, 64, 3, false, false>(A, B, p, splits, st) : launch_tc<32, 32, 6, false, false>(A, B, p, splits, st);
 }
 
 // Tuning cache: one entry per GEMM shape class; filled the first time a shape is seen outside
@@ -834,8 +885,9 @@ static std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int>, int> 
 
 static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const Params& p, int splits, int BN,
                               bool plain, cudaStream_t st) {
-  const Config* cands = plain ? (BN == 64 ? kPlainCfg64 : kPlainCfg32)
-                              : (BN == 128 ? kSplitCfg128 : BN == 64 ? kSplitCfg64 : kSplitCfg32);
+  const Config* cands = plain    ? (BN == 64 ? kPlainCfg64 : kPlainCfg32)
+                        : A.eight ? (BN == 64 ? kSplit8Cfg64 : kSplit8Cfg32)
+                                  : (BN == 128 ? kSplitCfg128 : BN == 64 ? kSplitCfg64 : kSplitCfg32);
   const int ncand = 2;
   const char* force = getenv("LRTEI_TC_CONFIG");
   if (force && *force) {
@@ -843,7 +895,7 @@ static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const 
     ProfScope ps("tc_gemm", st);
     return launch_cfg(A, B, p, splits, plain, cands[(i < 0 || i >= ncand) ? 0 : i], st);
   }
-  const auto key = std::make_tuple(p.M, p.N, A.kpad, splits, (int)plain, p.symmetric, p.transpose_out);
+  const auto key = std::make_tuple(p.M, p.N, A.kpad, splits, (int)plain + 2 * (int)A.eight, p.symmetric, p.transpose_out);
   int choice = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -917,7 +969,7 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
   // its operand reads from shared memory); narrow outputs take narrower tiles.  Plain BF16 keeps
   // 64-column tiles.
   const bool plain_ops = A.plain;
-  const int BN = (N <= 32) ? 32 : (N <= 64 || plain_ops) ? 64 : 128;
+  const int BN = (N <= 32) ? 32 : (N <= 64 || plain_ops || A.eight) ? 64 : 128;
   const int64_t tiles_m = (M + tc::BM - 1) / tc::BM, tiles_n = (N + BN - 1) / BN;
   p.tiles_m = tiles_m;
   p.tiles_n = tiles_n;
@@ -941,8 +993,12 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
     p.split_stride = 0;
   }
   const bool plain = A.plain;
-  if (plain != B.plain) {
-    set_error("tc_gemm: operands must both be plain or both split");
+  if (plain != B.plain || A.eight != B.eight) {
+    set_error("tc_gemm: operands must share one precision scheme");
+    return LRTEI_ERR_ARG;
+  }
+  if (A.eight && !A.s1h) {
+    set_error("tc_gemm: the eight-product scheme needs the A operand's t1 / 2^11 plane");
     return LRTEI_ERR_ARG;
   }
   lrtei_status s = tc::run_tuned(A, B, p, splits, BN, plain, st);

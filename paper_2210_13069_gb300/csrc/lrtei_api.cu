@@ -184,7 +184,7 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   if (n < 1 || n > kMaxN) { set_error("n must be in 1..%d (got %d)", kMaxN, n); return LRTEI_ERR_ARG; }
   if (P < 1 || P > kMaxP) { set_error("P must be in 1..%d (got %d)", kMaxP, P); return LRTEI_ERR_ARG; }
   if ((box_lo == nullptr) != (box_hi == nullptr)) { set_error("box_lo and box_hi must both be given or both NULL"); return LRTEI_ERR_ARG; }
-  if (precision < LRTEI_FP64 || precision > LRTEI_BF16) { set_error("unknown precision %d", (int)precision); return LRTEI_ERR_ARG; }
+  if (precision < LRTEI_FP64 || precision > LRTEI_SPLIT_F16_8) { set_error("unknown precision %d", (int)precision); return LRTEI_ERR_ARG; }
   int ndev = 0;
   cudaError_t ce = cudaGetDeviceCount(&ndev);
   if (ce != cudaSuccess || ndev == 0) {
@@ -411,19 +411,23 @@ lrtei_status ensure_F32(lrtei_plan* pl, cudaStream_t st) {
   return finish_launch("build_F32");
 }
 
-bool is_split(const lrtei_plan* pl) { return pl->prec == LRTEI_SPLIT_F16 || pl->prec == LRTEI_BF16; }
+bool is_split(const lrtei_plan* pl) {
+  return pl->prec == LRTEI_SPLIT_F16 || pl->prec == LRTEI_SPLIT_F16_8 || pl->prec == LRTEI_BF16;
+}
+bool eight_products(const lrtei_plan* pl) { return pl->prec == LRTEI_SPLIT_F16_8; }
 int nslices(const lrtei_plan* pl) { return pl->prec == LRTEI_BF16 ? 1 : 3; }
 
 lrtei_status alloc_split(lrtei_plan* pl, SplitMatrix& m, int64_t rows, int64_t k, bool with_s1h) {
   m.rows = rows;
   m.kpad = kpad256(k);
   m.plain = pl->prec == LRTEI_BF16;
+  m.eight = eight_products(pl);
   const size_t cnt = (size_t)rows * m.kpad;
   LRTEI_TRY(pl->alloc(&m.s0, cnt));
   if (!m.plain) {
     LRTEI_TRY(pl->alloc(&m.s1, cnt));
     LRTEI_TRY(pl->alloc(&m.s2, cnt));
-    if (with_s1h) LRTEI_TRY(pl->alloc(&m.s1h, cnt));
+    if (with_s1h || m.eight) LRTEI_TRY(pl->alloc(&m.s1h, cnt));
   }
   LRTEI_TRY(pl->alloc(&m.expo, rows));
   return LRTEI_OK;
@@ -541,16 +545,17 @@ lrtei_status ensure_jbuild_operands(lrtei_plan* pl, cudaStream_t st) {
 }
 
 // A scratch split operand (planes owned by the call).
-lrtei_status scratch_split(Scratch& sc, SplitMatrix& m, int64_t rows, int64_t k, bool with_s1h, bool plain) {
+lrtei_status scratch_split(Scratch& sc, SplitMatrix& m, int64_t rows, int64_t k, bool with_s1h, const lrtei_plan* pl) {
   m.rows = rows;
   m.kpad = kpad256(k);
-  m.plain = plain;
+  m.plain = pl->prec == LRTEI_BF16;
+  m.eight = eight_products(pl);
   const size_t cnt = (size_t)rows * m.kpad;
   LRTEI_TRY(sc.get(&m.s0, cnt));
-  if (!plain) {
+  if (!m.plain) {
     LRTEI_TRY(sc.get(&m.s1, cnt));
     LRTEI_TRY(sc.get(&m.s2, cnt));
-    if (with_s1h) LRTEI_TRY(sc.get(&m.s1h, cnt));
+    if (with_s1h || m.eight) LRTEI_TRY(sc.get(&m.s1h, cnt));
   }
   LRTEI_TRY(sc.get(&m.expo, rows));
   return LRTEI_OK;
@@ -580,7 +585,7 @@ lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int
   Fr.expo += r0;
   LRTEI_TRY(tc_gemm(Fr, pl->Ksp, nr, n3, 1.0, G, n3, false, false, 1, nullptr, pl->d_status, st));
   SplitMatrix Gs;
-  LRTEI_TRY(scratch_split(sc, Gs, nr, n3, false, pl->prec == LRTEI_BF16));
+  LRTEI_TRY(scratch_split(sc, Gs, nr, n3, false, pl));
   {
     ProfScope ps("split", st);
     launch_split_rows(G, nr, n3, n3, Gs, false, nslices(pl), st);
@@ -871,9 +876,9 @@ static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double
   const int smax = std::max(s1, std::max(s2, s3));
   LRTEI_TRY(sc.get(&part, (size_t)smax * std::max(n3, npair) * R));
   SplitMatrix Dsp, Xsp, Ysp;
-  LRTEI_TRY(scratch_split(sc, Dsp, R, npair, true, plan->prec == LRTEI_BF16));
-  LRTEI_TRY(scratch_split(sc, Xsp, R, n3, true, plan->prec == LRTEI_BF16));
-  LRTEI_TRY(scratch_split(sc, Ysp, R, n3, true, plan->prec == LRTEI_BF16));
+  LRTEI_TRY(scratch_split(sc, Dsp, R, npair, true, plan));
+  LRTEI_TRY(scratch_split(sc, Xsp, R, n3, true, plan));
+  LRTEI_TRY(scratch_split(sc, Ysp, R, n3, true, plan));
   launch_pack_density(nbf, R, d_D, Du, st);
   launch_transpose(Du, npair, R, R, DuT, npair, st);
   {

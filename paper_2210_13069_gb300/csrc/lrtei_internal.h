@@ -132,6 +132,7 @@ struct SplitMatrix {  // row-major rows x kpad, three FP16 integer slices + per-
   uint16_t* s1h = nullptr; // second slice t1 pre-scaled by 2^-11 (B operand only)
   int* expo = nullptr;     // [rows]
   bool plain = false;      // plain BF16 operands in s0 only (no slices)
+  bool eight = false;      // eight-product scheme: every operand carries s1h (A: t1 t2 products)
 };
 // Slice an FP64 row-major matrix (rows x k, ld) into a SplitMatrix (zero padded to kpad).
 void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld, SplitMatrix& m, bool with_s1h,

@@ -19,10 +19,11 @@ _SO = os.path.join(_HERE, "_build", "liblrtei.so")
 LRTEI_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NUMERIC",
                 6: "ERR_UNSUPPORTED"}
-LRTEI_FP64, LRTEI_FP32, LRTEI_SPLIT_F16, LRTEI_BF16 = 0, 1, 2, 3
+LRTEI_FP64, LRTEI_FP32, LRTEI_SPLIT_F16, LRTEI_BF16, LRTEI_SPLIT_F16_8 = 0, 1, 2, 3, 4
 LRTEI_FORM_AUTO, LRTEI_FORM_HADAMARD, LRTEI_FORM_FACTORED = 0, 1, 2
 
-PRECISIONS = {"fp64": LRTEI_FP64, "fp32": LRTEI_FP32, "split_f16": LRTEI_SPLIT_F16, "bf16": LRTEI_BF16}
+PRECISIONS = {"fp64": LRTEI_FP64, "fp32": LRTEI_FP32, "split_f16": LRTEI_SPLIT_F16, "bf16": LRTEI_BF16,
+              "split_f16_8": LRTEI_SPLIT_F16_8}
 FORMS = {"auto": LRTEI_FORM_AUTO, "hadamard": LRTEI_FORM_HADAMARD, "factored": LRTEI_FORM_FACTORED}
 
 

@@ -205,6 +205,41 @@ def test_split_f16_full_B(lib, maker):
     assert np.array_equal(B, B.T)
 
 
+@pytest.mark.parametrize("maker", ["small_s", "spd_small", "ragged"])
+def test_split_f16_8_full_B(lib, maker):
+    """Eight products in three accumulators (the next-order slice products kept, the small terms
+    accumulated at their own scale): rel. Frobenius <= 1e-8, B exactly symmetric."""
+    m = {"small_s": synth.workload_small_s, "spd_small": mol_spd_small, "ragged": mol_ragged}[maker]()
+    ref = oracle.Oracle.from_molecule(m).assemble_B()
+    pl = lib.Plan(m, "split_f16_8")
+    B = pl.assemble_B("auto").cpu().numpy()
+    pl.status()
+    err = rel_fro(B, ref)
+    print(f"split_f16_8 {maker}: N_b={m.nbf} rel. Frobenius error {err:.3e}")
+    assert err <= 1e-8
+    assert np.array_equal(B, B.T)
+
+
+@pytest.mark.parametrize("cfg", ["0", "1"])
+def test_split_f16_8_each_tile_config_and_jbuild(lib, cfg, monkeypatch):
+    """The eight-product kernel configurations (128x64 tiles for B and for J-builds of 40
+    densities, 128x32 for 7 densities, both K depths) on the ragged 45-function instance."""
+    import torch
+    monkeypatch.setenv("LRTEI_TC_CONFIG", cfg)
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    pl = lib.Plan(m, "split_f16_8")
+    B = pl.assemble_B().cpu().numpy()
+    pl.status()
+    assert rel_fro(B, o.assemble_B()) <= 1e-8
+    for R in (40, 7):
+        D = synth.random_densities(14, m.nbf, R)
+        J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+        err = rel_fro(J, o.jbuild_factored(D))
+        print(f"split_f16_8 J-build R={R}: {err:.3e}")
+        assert err <= 1e-8, R
+
+
 @pytest.mark.parametrize("maker", ["spd_small", "ragged"])
 def test_plain_bf16_error_stated(lib, maker):
     """Plain BF16 operands with FP32 accumulation: rel. Frobenius <= 1e-3."""
@@ -292,7 +327,7 @@ def test_split_f16_each_tile_config(lib, cfg, monkeypatch):
         assert rel_fro(J, o.jbuild_factored(D)) <= 1e-7, R
 
 
-@pytest.mark.parametrize("precision", ["fp64", "split_f16"])
+@pytest.mark.parametrize("precision", ["fp64", "split_f16", "split_f16_8"])
 def test_assemble_B_into_pinned_host_memory(lib, precision):
     """B written by the device straight into pinned host memory equals B in device memory, bit
     for bit; pageable host memory is refused before any launch."""
