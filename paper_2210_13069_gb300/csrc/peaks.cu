@@ -7,8 +7,8 @@
 namespace lrtei {
 
 namespace {
-constexpr int kChains = 8;
-constexpr int kUnroll = 16;
+constexpr int kChains = 16;
+constexpr int kUnroll = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fma_rate(int iters, T seed, T* __restrict__ out) {
