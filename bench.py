@@ -466,6 +466,29 @@ def run_ours(args, world, rank, local):
     if not args.no_batched and args.precision in ("split_f16", "split_f16_8", "bf16"):
         batched = run_batched(args, world)
 
+    # ---- the 20-function s-only instance: latency of one full 400 x 400 B (plan resident)
+    nb20 = None
+    if args.natoms == 12 and not args.no_fp64:
+        m20 = synth.workload_small_s()
+        nb20 = {"workload": "nb20_s: 4 atoms, 5 s functions each, omega=0.5, n=16, P=20; 400x400 B"}
+        for prec in ("fp64", args.precision):
+            p20 = lrtei.Plan(m20, prec)
+            B20 = torch.empty((400, 400), dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                p20.assemble_B("auto", out=B20)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(10):
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                p20.assemble_B("auto", out=B20)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a0.elapsed_time(a1))
+            nb20[f"{prec}_ms_median"] = statistics.median(ts)
+            p20.close()
+
     # ---- the 360-function instance (24 atoms, omega = 0.33): full 129 600^2 B (134 GB) per step.
     # Six products measured 1.06e-7 on sampled rows of it: it runs the eight-product scheme.
     nb360 = None
@@ -517,7 +540,7 @@ def run_ours(args, world, rank, local):
                        "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
-            "jbuilds": jb, "fp64_same_gpu": fp64, "split_f16_8": split8, "batched": batched, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "jbuilds": jb, "fp64_same_gpu": fp64, "split_f16_8": split8, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)
