@@ -60,11 +60,9 @@ def test_adam_training_fits_a_smooth_map(lib):
     assert hist[-1] < 2e-3
 
 
-def test_selector_meets_target_and_gains_over_fixed(lib, tmp_path):
-    """Train on sweeps, then on held-out instances: the chosen (n, P) reaches the requested error
-    in at least 90 % of the reachable cases, and where the fixed (32, 48) also reaches it the
-    chosen one is cheaper on average (cost ~ n^3 per J-build)."""
-    import torch
+@pytest.fixture(scope="module")
+def trained(lib):
+    """The selector trained on 160 error sweeps (about a minute on the GPU)."""
     from paper_2210_13069_gb300 import selector as S
     train = [S.sweep(10_000 + i) for i in range(160)]
     X, Y = S.dataset(train)
@@ -72,6 +70,16 @@ def test_selector_meets_target_and_gains_over_fixed(lib, tmp_path):
     sel = S.Selector(64, seed=11)
     hist = sel.train(X, Y, epochs=250, batch=256, lr=2e-3)
     assert hist[-1] < hist[0]
+    return sel, X, train
+
+
+def test_selector_meets_target_and_gains_over_fixed(lib, trained, tmp_path):
+    """On held-out instances: the chosen (n, P) reaches the requested error in at least 90 % of
+    the reachable cases, and where the fixed (32, 48) also reaches it the chosen one is cheaper
+    on average (cost ~ n^3 per J-build)."""
+    import torch
+    from paper_2210_13069_gb300 import selector as S
+    sel, X, train = trained
     met = tried = 0
     gains, fixed_fail = [], 0
     for i in range(16):
@@ -101,3 +109,4 @@ def test_selector_meets_target_and_gains_over_fixed(lib, tmp_path):
     sel.save(p, meta={"sweeps": len(train)})
     sel2 = S.Selector.load(p)
     assert np.array_equal(sel.predict_raw(X[:50]), sel2.predict_raw(X[:50]))
+
