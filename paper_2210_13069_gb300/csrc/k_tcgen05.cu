@@ -18,14 +18,15 @@
 // t1 t2 and t2 t1 as well and splits L12 into L1 = s0 t1 + t1 s0 and L2 (the rest, in its own
 // accumulator): three accumulators per buffer, 128 x 64 tiles, C from T0 + (T1 + T2) / 2^11.
 //
-// Kernel organisation (one 128 x BN output tile per CTA, BN = 128 for wide outputs):
+// Kernel organisation (persistent: one CTA per SM walks 128 x BN output tiles, BN = 128 for
+// wide outputs, 18 warps):
 //   warp 0       TMA producer: 3 A slices + 4 B slices per 64- or 32-deep K step into a ring
 //                of shared-memory stages (128- or 64-byte swizzle), mbarrier transaction counts
 //   warp 1       TMEM allocation (512 columns) and the single MMA-issuing thread:
 //                6 tcgen05.mma (M=128, N=BN, K=16) per 16-deep k step into two accumulators,
 //                double-buffered across K chunks, grouped by A slice (collector reuse)
-//   warps 2..    epilogue (16 warps, 8 for BN = 128): tcgen05.ld of each finished chunk,
-//                running sums, staged FP64 store
+//   warps 2..17  epilogue: tcgen05.ld of each finished chunk, running sums, the finished tile
+//                staged through the idle ring and stored coalesced
 // A 128 x 64 MMA is bound by its operand reads from shared memory (2/3 of the tensor rate
 // measured); from N = 128 on the pipe runs at its full rate.
 // Every mbarrier wait is bounded: on expiry the CTA raises the device status word, stops
@@ -53,12 +54,10 @@ constexpr int KCHUNK = 256;  // K per exact FP32 accumulation chunk
 // swizzle, smaller stages so more of them fit in shared memory).
 constexpr int NA = 3;        // A slices: s0, t1, t2'
 constexpr int NB = 4;        // B slices: s0, t1, t1', t2'
-// Epilogue warps: 4 per TMEM lane quadrant for tiles up to 64 columns; 2 per quadrant for
-// 128-column tiles, whose running sums (two words per element, 128 per thread) need the larger
-// per-thread register share of a 10-warp block (measured slightly faster than 16 warps with
-// 64 sums each).
+// Epilogue warps: 4 per TMEM lane quadrant, each draining BN/4 columns of its 32 lanes per
+// chunk (two running sums per element: 64 registers a thread at BN = 128; 96 available).
 template <int BN>
-__host__ __device__ constexpr int epi_warps() { return BN >= 128 ? 8 : 16; }
+__host__ __device__ constexpr int epi_warps() { return 16; }
 template <int BN>
 __host__ __device__ constexpr int block_threads() { return 64 + 32 * epi_warps<BN>(); }  // producer, MMA, epilogue
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -80,6 +79,7 @@ struct Params {
   int64_t split_stride;   // elements between split partials (splits > 1)
   int transpose_out;
   int symmetric;
+  int splits;
   int* status;
 };
 
@@ -272,46 +272,25 @@ __device__ __forceinline__ double tile_value(const int* st0, const float* st12, 
   return scale == 1.0 ? v : scale * v;
 }
 
-// ------------------------------------------------------------------ the kernel
-// PLAIN: one BF16 operand plane each, one product per k step, FP32 sums (no exactness).
-// P8: eight products per k step (the next-order terms t1 t2' / 2^11 and t2' t1 / 2^11 kept, with
-// a fourth A slice t1 / 2^11) into three accumulators.
-template <int BN, int BK, int STAGES, bool PLAIN, bool P8>
-__global__ void __launch_bounds__(block_threads<BN>(), 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
-              const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap ta1h,
-              const __grid_constant__ CUtensorMap tb0, const __grid_constant__ CUtensorMap tb1,
-              const __grid_constant__ CUtensorMap tb1h, const __grid_constant__ CUtensorMap tb2, const Params p) {
-  constexpr uint32_t A_BYTES = BM * BK * 2;
-  constexpr uint32_t B_BYTES = BN * BK * 2;
-  constexpr int NA_ = PLAIN ? 1 : (P8 ? NA + 1 : NA), NB_ = PLAIN ? 1 : NB;
-  constexpr uint32_t STAGE_BYTES = NA_ * A_BYTES + NB_ * B_BYTES;
-  constexpr int KSTEPS = KCHUNK / BK;  // pipeline stages per chunk
-  constexpr int QC = BN / (epi_warps<BN>() / 4);  // columns per epilogue thread
-  constexpr int NACC = P8 ? 3 : 2;                 // accumulators per buffer: L0, L12 (L1, L2 if P8)
-  static_assert(2 * NACC * BN <= 512, "two buffers of the accumulators must fit in TMEM");
+// One work item of the persistent grid: an output tile and a K range.
+struct Work {
+  int64_t m0, n0;
+  int c_begin, nchunks;
+  int split;
+  bool mirror;  // strictly above the diagonal block of a symmetric product: write C^T too
+};
 
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 4 * (P8 ? 3 : 2) + (BM + BN) * 4;
-  constexpr uint32_t RING_BYTES = (STAGES * STAGE_BYTES > TILE_BYTES) ? STAGES * STAGE_BYTES : TILE_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ((RING_BYTES + 7) & ~7u));
-  uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;   // [2] accumulator buffer ready
-  uint64_t* acce = accf + 2;         // [2] accumulator buffer drained
-  uint64_t* done = acce + 2;         // all MMAs retired
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  // tile coordinates
+// Item -> tile.  Items are split-major, so the ~152 items running at once belong to one split
+// and share operand slabs in L2: tiles are walked in groups of kGroupM M-tiles (M fastest inside
+// a group); the symmetric product walks the upper triangle of 128x128 blocks in groups of
+// kGroupRows block rows, column by column.
+template <int BN>
+__device__ __forceinline__ Work work_item(const Params& p, int64_t item) {
+  Work w;
+  const int64_t tile = item % p.ntiles;
+  w.split = (int)(item / p.ntiles);
   int64_t ti, tj;
-  const int64_t tile = blockIdx.x;
-  // Tile order: the ~152 CTAs resident at once should share operand slabs in L2, so tiles are
-  // walked in groups of kGroupM M-tiles (M fastest inside a group).  The symmetric product walks
-  // the upper triangle of 128x128 blocks in groups of kGroupRows block rows, column by column.
-  bool mirror_tile = false;
+  w.mirror = false;
   if (p.symmetric) {
     constexpr int SUB = BM / BN;
     const int64_t nb = (p.tiles_n + SUB - 1) / SUB;  // 128x128 blocks per side
@@ -331,7 +310,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     }
     ti = r;
     tj = c * SUB + sub;
-    mirror_tile = c != r;  // strictly above the diagonal block: write the transpose too
+    w.mirror = c != r;
   } else {
     const int64_t per_group = (int64_t)kGroupM * p.tiles_n;
     const int64_t first_m = (tile / per_group) * kGroupM;
@@ -340,11 +319,53 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     ti = first_m + in_g % gsize;
     tj = in_g / gsize;
   }
-  const int64_t m0 = ti * BM, n0 = tj * BN;
-  const int split = blockIdx.y;
-  const int c_begin = split * p.chunks_per_split;
-  const int c_end = min(p.nchunks_total, c_begin + p.chunks_per_split);
-  const int nchunks = max(0, c_end - c_begin);
+  w.m0 = ti * BM;
+  w.n0 = tj * BN;
+  w.c_begin = w.split * p.chunks_per_split;
+  w.nchunks = max(0, min(p.nchunks_total, w.c_begin + p.chunks_per_split) - w.c_begin);
+  return w;
+}
+
+// ------------------------------------------------------------------ the kernel
+// Persistent: CTA b walks the items b, b + gridDim.x, ...  The producer, the MMA thread and the
+// epilogue warps keep running counters of k steps and chunks across items, so the ring stages
+// and the two accumulator buffers flow from one tile to the next.  A finished tile is staged
+// through the ring's shared memory (idle then: the producer waits for the epilogue's "staged
+// tile stored" barrier before it loads the next tile), then stored coalesced.
+// PLAIN: one BF16 operand plane each, one product per k step, FP32 sums (no exactness).
+// P8: eight products per k step (the next-order terms t1 t2' / 2^11 and t2' t1 / 2^11 kept, with
+// a fourth A slice t1 / 2^11) into three accumulators.
+template <int BN, int BK, int STAGES, bool PLAIN, bool P8>
+__global__ void __launch_bounds__(block_threads<BN>(), 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
+              const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap ta1h,
+              const __grid_constant__ CUtensorMap tb0, const __grid_constant__ CUtensorMap tb1,
+              const __grid_constant__ CUtensorMap tb1h, const __grid_constant__ CUtensorMap tb2, const Params p) {
+  constexpr uint32_t A_BYTES = BM * BK * 2;
+  constexpr uint32_t B_BYTES = BN * BK * 2;
+  constexpr int NA_ = PLAIN ? 1 : (P8 ? NA + 1 : NA), NB_ = PLAIN ? 1 : NB;
+  constexpr uint32_t STAGE_BYTES = NA_ * A_BYTES + NB_ * B_BYTES;
+  constexpr int KSTEPS = KCHUNK / BK;  // pipeline stages per chunk
+  constexpr int QC = BN / (epi_warps<BN>() / 4);  // columns per epilogue thread
+  constexpr int NACC = P8 ? 3 : 2;                 // accumulators per buffer: L0, L12 (L1, L2 if P8)
+  static_assert(2 * NACC * BN <= 512, "two buffers of the accumulators must fit in TMEM");
+  constexpr int NE = 32 * epi_warps<BN>();
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 4 * (P8 ? 3 : 2) + (BM + BN) * 4;
+  constexpr uint32_t RING_BYTES = (STAGES * STAGE_BYTES > TILE_BYTES) ? STAGES * STAGE_BYTES : TILE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ((RING_BYTES + 7) & ~7u));
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;   // [2] accumulator buffer ready
+  uint64_t* acce = accf + 2;         // [2] accumulator buffer drained
+  uint64_t* done = acce + 2;         // all MMAs retired
+  uint64_t* tstored = done + 1;      // the staged tile was stored: the ring may be refilled
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tstored + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nitems = p.ntiles * (int64_t)p.splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -356,6 +377,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       mbar_init(&acce[b], epi_warps<BN>());
     }
     mbar_init(done, 1);
+    mbar_init(tstored, epi_warps<BN>());
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -372,34 +394,42 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      const int nk = nchunks * KSTEPS;
-      int issued = 0;
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, 32)) break;
-        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-        uint8_t* st = smem + (size_t)s * STAGE_BYTES;
-        const int kx = (c_begin * KSTEPS + it) * BK;
-        uint8_t* sb = st + NA_ * A_BYTES;
-        tma_load_2d(&ta0, st + 0 * A_BYTES, &full[s], kx, (int)m0);
-        tma_load_2d(&tb0, sb + 0 * B_BYTES, &full[s], kx, (int)n0);
-        if constexpr (!PLAIN) {
-          tma_load_2d(&ta1, st + 1 * A_BYTES, &full[s], kx, (int)m0);
-          tma_load_2d(&ta2, st + 2 * A_BYTES, &full[s], kx, (int)m0);
-          tma_load_2d(&tb1, sb + 1 * B_BYTES, &full[s], kx, (int)n0);
-          tma_load_2d(&tb1h, sb + 2 * B_BYTES, &full[s], kx, (int)n0);
-          tma_load_2d(&tb2, sb + 3 * B_BYTES, &full[s], kx, (int)n0);
-          if constexpr (P8) tma_load_2d(&ta1h, st + 3 * A_BYTES, &full[s], kx, (int)m0);
+      uint32_t it = 0, ntile = 0;  // k steps issued, items started by this CTA
+      bool stop = false;
+      for (int64_t item = blockIdx.x; item < nitems && !stop; item += gridDim.x, ++ntile) {
+        if (ntile > 0) {
+          // the previous tile is staged in the ring's memory until the epilogue has stored it
+          if (!mbar_wait(tstored, (ntile - 1) & 1u, abort_flag, p.status, 64)) break;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        issued = it + 1;
+        const Work w = work_item<BN>(p, item);
+        const int nk = w.nchunks * KSTEPS;
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, 32)) { stop = true; break; }
+          mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          uint8_t* st = smem + (size_t)s * STAGE_BYTES;
+          const int kx = (w.c_begin * KSTEPS + kk) * BK;
+          uint8_t* sb = st + NA_ * A_BYTES;
+          tma_load_2d(&ta0, st + 0 * A_BYTES, &full[s], kx, (int)w.m0);
+          tma_load_2d(&tb0, sb + 0 * B_BYTES, &full[s], kx, (int)w.n0);
+          if constexpr (!PLAIN) {
+            tma_load_2d(&ta1, st + 1 * A_BYTES, &full[s], kx, (int)w.m0);
+            tma_load_2d(&ta2, st + 2 * A_BYTES, &full[s], kx, (int)w.m0);
+            tma_load_2d(&tb1, sb + 1 * B_BYTES, &full[s], kx, (int)w.n0);
+            tma_load_2d(&tb1h, sb + 2 * B_BYTES, &full[s], kx, (int)w.n0);
+            tma_load_2d(&tb2, sb + 3 * B_BYTES, &full[s], kx, (int)w.n0);
+            if constexpr (P8) tma_load_2d(&ta1h, st + 3 * A_BYTES, &full[s], kx, (int)w.m0);
+          }
+        }
       }
       // On abort, wait (bounded) for the loads still in flight before the CTA can exit.
       if (*abort_flag) {
-        for (int it = max(0, issued - STAGES); it < issued; ++it) {
-          const int s = it % STAGES;
+        for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0u); j < it; ++j) {
+          const int s = (int)(j % STAGES);
           long long t0 = clock64();
-          while (!mbar_try_wait(&full[s], (uint32_t)(it / STAGES) & 1u) && clock64() - t0 < kWaitCycles) {
+          while (!mbar_try_wait(&full[s], (j / STAGES) & 1u) && clock64() - t0 < kWaitCycles) {
           }
         }
       }
@@ -408,53 +438,56 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = instr_desc<BN, PLAIN>();
+      uint32_t it = 0, cg = 0;  // k steps and chunks consumed, across items
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int buf = c & 1;
-        if (!mbar_wait(&acce[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t d0 = tmem_base + (uint32_t)(buf * NACC * BN);
-        const uint32_t d1 = d0 + BN;
-        const uint32_t d2 = P8 ? d0 + 2 * BN : d1;
-        for (int step = 0; step < KSTEPS; ++step) {
-          const int it = c * KSTEPS + step;
-          const int s = it % STAGES;
-          if (!mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1u, abort_flag, p.status)) { ok = false; break; }
+      for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        const Work w = work_item<BN>(p, item);
+        for (int c = 0; c < w.nchunks && ok; ++c, ++cg) {
+          const int buf = (int)(cg & 1u);
+          if (!mbar_wait(&acce[buf], ((cg >> 1) & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
-          const uint64_t a0 = smem_desc<BK>(base), a1 = smem_desc<BK>(base + A_BYTES),
-                         a2 = smem_desc<BK>(base + 2 * A_BYTES), a1h = smem_desc<BK>(base + 3 * A_BYTES);
-          const uint32_t bb = base + NA_ * A_BYTES;
-          const uint64_t b0 = smem_desc<BK>(bb), b1 = smem_desc<BK>(bb + B_BYTES), b1h = smem_desc<BK>(bb + 2 * B_BYTES),
-                         b2 = smem_desc<BK>(bb + 3 * B_BYTES);
+          const uint32_t d0 = tmem_base + (uint32_t)(buf * NACC * BN);
+          const uint32_t d1 = d0 + BN;
+          const uint32_t d2 = P8 ? d0 + 2 * BN : d1;
+          for (int step = 0; step < KSTEPS; ++step, ++it) {
+            const int s = (int)(it % STAGES);
+            if (!mbar_wait(&full[s], (it / STAGES) & 1u, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
+            const uint64_t a0 = smem_desc<BK>(base), a1 = smem_desc<BK>(base + A_BYTES),
+                           a2 = smem_desc<BK>(base + 2 * A_BYTES), a1h = smem_desc<BK>(base + 3 * A_BYTES);
+            const uint32_t bb = base + NA_ * A_BYTES;
+            const uint64_t b0 = smem_desc<BK>(bb), b1 = smem_desc<BK>(bb + B_BYTES),
+                           b1h = smem_desc<BK>(bb + 2 * B_BYTES), b2 = smem_desc<BK>(bb + 3 * B_BYTES);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            const uint64_t o = (uint64_t)((k * 32) >> 4);  // +32 bytes along K inside the swizzle atom
-            const uint32_t first = (step == 0 && k == 0) ? 0u : 1u;
-            if constexpr (PLAIN) {
-              mma_bf16(d0, a0 + o, b0 + o, idesc, first);
-            } else {
-              // grouped by A slice so that each is read from shared memory once per k step
-              // P8: L1 = s0 t1 + t1 s0 in d1, the smaller terms in their own accumulator d2, so
-              // that the tensor core's truncating FP32 accumulation cuts them at their own scale
-              mma_bf16_a<ACol::fill>(d0, a0 + o, b0 + o, idesc, first);
-              mma_bf16_a<ACol::use>(d1, a0 + o, b1 + o, idesc, first);
-              mma_bf16_a<ACol::lastuse>(d2, a0 + o, b2 + o, idesc, P8 ? first : 1u);
-              mma_bf16_a<ACol::fill>(d1, a1 + o, b0 + o, idesc, 1u);
-              mma_bf16_a<ACol::lastuse>(d2, a1 + o, b1h + o, idesc, 1u);
-              if constexpr (P8) {
-                mma_bf16_a<ACol::fill>(d2, a2 + o, b0 + o, idesc, 1u);
-                mma_bf16_a<ACol::lastuse>(d2, a2 + o, b1h + o, idesc, 1u);  // t2' t1 / 2^11
-                mma_bf16(d2, a1h + o, b2 + o, idesc, 1u);                  // t1 / 2^11 t2'
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t o = (uint64_t)((k * 32) >> 4);  // +32 bytes along K inside the swizzle atom
+              const uint32_t first = (step == 0 && k == 0) ? 0u : 1u;
+              if constexpr (PLAIN) {
+                mma_bf16(d0, a0 + o, b0 + o, idesc, first);
               } else {
-                mma_bf16(d1, a2 + o, b0 + o, idesc, 1u);
+                // grouped by A slice so that each is read from shared memory once per k step
+                // P8: L1 = s0 t1 + t1 s0 in d1, the smaller terms in their own accumulator d2, so
+                // that the tensor core's truncating FP32 accumulation cuts them at their own scale
+                mma_bf16_a<ACol::fill>(d0, a0 + o, b0 + o, idesc, first);
+                mma_bf16_a<ACol::use>(d1, a0 + o, b1 + o, idesc, first);
+                mma_bf16_a<ACol::lastuse>(d2, a0 + o, b2 + o, idesc, P8 ? first : 1u);
+                mma_bf16_a<ACol::fill>(d1, a1 + o, b0 + o, idesc, 1u);
+                mma_bf16_a<ACol::lastuse>(d2, a1 + o, b1h + o, idesc, 1u);
+                if constexpr (P8) {
+                  mma_bf16_a<ACol::fill>(d2, a2 + o, b0 + o, idesc, 1u);
+                  mma_bf16_a<ACol::lastuse>(d2, a2 + o, b1h + o, idesc, 1u);  // t2' t1 / 2^11
+                  mma_bf16(d2, a1h + o, b2 + o, idesc, 1u);                  // t1 / 2^11 t2'
+                } else {
+                  mma_bf16(d1, a2 + o, b0 + o, idesc, 1u);
+                }
               }
             }
+            mma_commit(&empty[s]);  // stage s may be refilled once these MMAs retire
           }
-          mma_commit(&empty[s]);  // stage s may be refilled once these MMAs retire
+          if (!ok) break;
+          mma_commit(&accf[buf]);
         }
-        if (!ok) break;
-        mma_commit(&accf[buf]);
       }
       // retire every MMA this thread issued before TMEM is released
       mma_commit(done);
@@ -468,86 +501,84 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     const int quad = warp & 3;             // TMEM lane quadrant this warp may access
     const int col0 = (ew >> 2) * QC;       // first column of this thread
     const int row = quad * 32 + lane;      // row inside the tile
-    int T0[QC];
-    float T12[QC];
-    float T2[P8 ? QC : 1];
-#pragma unroll
-    for (int j = 0; j < QC; ++j) {
-      T0[j] = 0;
-      T12[j] = 0.f;
-      if constexpr (P8) T2[j] = 0.f;
-    }
-    bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int buf = c & 1;
-      // one lane waits, the warp reconverges before the .sync.aligned TMEM loads
-      int got = 1;
-      if (lane == 0) got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, abort_flag, p.status, 128) ? 1 : 0;
-      got = __shfl_sync(0xffffffffu, got, 0);
-      if (!got) { ok = false; break; }
-      tc_fence_after();
-      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * NACC * BN + col0);
-      // both accumulators' loads of an 8-column group are in flight together (one wait per group)
-#pragma unroll
-      for (int j0 = 0; j0 < QC; j0 += 8) {
-        uint32_t r[8], q[8];
-        tmem_ld8(tbase + j0, r);
-        if constexpr (!PLAIN) tmem_ld8(tbase + BN + j0, q);
-        tmem_wait_ld();
-        if constexpr (PLAIN) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) T12[j0 + j] += __uint_as_float(r[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
-            T12[j0 + j] += __uint_as_float(q[j]);
-          }
-          if constexpr (P8) {
-            tmem_ld8(tbase + 2 * BN + j0, q);
-            tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 8; ++j) T2[j0 + j] += __uint_as_float(q[j]);
-          }
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[buf]);
-    }
-    // Stage the finished tile through the (now idle) operand shared memory: every MMA has
-    // retired once the last accumulator buffer was signalled, and every TMA load was consumed.
-    // The two running sums are staged as they are (32-bit words) and combined in FP64 by the
-    // store loop, so no thread holds its converted tile in registers.
-    constexpr int LDS = BN + 1;  // padded row stride (words) against bank conflicts
+    const int et = threadIdx.x - 64;       // 0..NE-1 over the epilogue warps
+    constexpr int LDS = BN + 1;            // padded row stride (words) against bank conflicts
     int* st0 = reinterpret_cast<int*>(smem);
     float* st12 = reinterpret_cast<float*>(st0 + BM * LDS);
     float* st2 = st12 + BM * LDS;  // P8 only
     int* sea = reinterpret_cast<int*>(st2 + (P8 ? BM * LDS : 0));
     int* seb = sea + BM;
-    const bool good = ok && !*abort_flag;
-    if (good) {
+    uint32_t cg = 0;                       // chunks drained, across items
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+      const Work w = work_item<BN>(p, item);
+      int T0[QC];
+      float T12[QC];
+      float T2[P8 ? QC : 1];
+#pragma unroll
+      for (int j = 0; j < QC; ++j) {
+        T0[j] = 0;
+        T12[j] = 0.f;
+        if constexpr (P8) T2[j] = 0.f;
+      }
+      for (int c = 0; c < w.nchunks; ++c, ++cg) {
+        const int buf = (int)(cg & 1u);
+        // one lane waits, the warp reconverges before the .sync.aligned TMEM loads
+        int got = 1;
+        if (lane == 0) got = mbar_wait(&accf[buf], (cg >> 1) & 1u, abort_flag, p.status, 128) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * NACC * BN + col0);
+        // both accumulators' loads of an 8-column group are in flight together (one wait per group)
+#pragma unroll
+        for (int j0 = 0; j0 < QC; j0 += 8) {
+          uint32_t r[8], q[8];
+          tmem_ld8(tbase + j0, r);
+          if constexpr (!PLAIN) tmem_ld8(tbase + BN + j0, q);
+          tmem_wait_ld();
+          if constexpr (PLAIN) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) T12[j0 + j] += __uint_as_float(r[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
+              T12[j0 + j] += __uint_as_float(q[j]);
+            }
+            if constexpr (P8) {
+              tmem_ld8(tbase + 2 * BN + j0, q);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) T2[j0 + j] += __uint_as_float(q[j]);
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[buf]);
+      }
+      if (!ok || *abort_flag) break;
+      // Every MMA of this tile has retired (its last accumulator buffer was signalled) and the
+      // producer loads nothing until this tile is stored: stage it through the ring's memory.
+      // The running sums are staged as 32-bit words and combined by the store loop.
 #pragma unroll
       for (int j = 0; j < QC; ++j) {
         st0[row * LDS + col0 + j] = T0[j];
         st12[row * LDS + col0 + j] = T12[j];
         if constexpr (P8) st2[row * LDS + col0 + j] = T2[j];
       }
-    }
-    constexpr int NE = 32 * epi_warps<BN>();
-    const int et = threadIdx.x - 64;  // 0..NE-1 over the epilogue warps
-    if (et < BM) sea[et] = (m0 + et < p.M) ? p.ea[m0 + et] : 0;
-    if (et < BN) seb[et] = (n0 + et < p.N) ? p.eb[n0 + et] : 0;
-    asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
-    if (good && !*abort_flag) {
-      double* Cs = p.C + (int64_t)split * p.split_stride;
+      if (et < BM) sea[et] = (w.m0 + et < p.M) ? p.ea[w.m0 + et] : 0;
+      if (et < BN) seb[et] = (w.n0 + et < p.N) ? p.eb[w.n0 + et] : 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
+      double* Cs = p.C + (int64_t)w.split * p.split_stride;
       // On a diagonal block of a symmetric product only the upper triangle (gm <= gn) is
       // kept and mirrored, so that C comes out exactly symmetric.
-      const bool diag = p.symmetric && !mirror_tile;
+      const bool diag = p.symmetric && !w.mirror;
       if (!p.transpose_out) {  // row-major: consecutive threads along a row
         for (int idx = et; idx < BM * BN; idx += NE) {
           const int r = idx / BN, c = idx % BN;
-          const int64_t gm = m0 + r, gn = n0 + c;
+          const int64_t gm = w.m0 + r, gn = w.n0 + c;
           if (gm < p.M && gn < p.N && (!diag || gm <= gn))
             Cs[gm * p.ldc + gn] = tile_value<PLAIN, P8>(st0, st12, st2, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
         }
@@ -555,11 +586,14 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       if (p.transpose_out || p.symmetric) {  // C^T: consecutive threads along a column of C
         for (int idx = et; idx < BM * BN; idx += NE) {
           const int c = idx / BM, r = idx % BM;
-          const int64_t gm = m0 + r, gn = n0 + c;
+          const int64_t gm = w.m0 + r, gn = w.n0 + c;
           if (gm < p.M && gn < p.N && (!diag || gm < gn))
             Cs[gn * p.ldc + gm] = tile_value<PLAIN, P8>(st0, st12, st2, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
         }
       }
+      // every epilogue thread has read the staged tile: the ring may be refilled
+      asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
+      if (lane == 0) mbar_arrive(tstored);
     }
   }
   __syncthreads();
@@ -797,7 +831,14 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
     if (e != cudaSuccess) return cuda_fail(e, "tc_gemm smem attribute");
     attr_set = true;
   }
-  dim3 grid((unsigned)p.ntiles, (unsigned)splits);
+  static int nsm = 0;  // persistent grid: one CTA per SM (shared memory and TMEM allow one)
+  if (nsm <= 0) {
+    int dev = 0;
+    LRTEI_CUDA(cudaGetDevice(&dev));
+    LRTEI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t nitems = p.ntiles * (int64_t)splits;
+  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(nitems, nsm)));
   count_launch();
   k_tc_gemm<BN, BK, STAGES, PLAIN, P8>
       <<<grid, block_threads<BN>(), smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], p);
@@ -965,6 +1006,7 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
   p.transpose_out = transpose_out ? 1 : 0;
   p.symmetric = symmetric_upper ? 1 : 0;
   p.status = d_status;
+  p.splits = splits;
   // Tile width: the tensor pipe runs at full rate from N = 128 on (a 128 x 64 MMA is bound by
   // its operand reads from shared memory); narrow outputs take narrower tiles.  Plain BF16 keeps
   // 64-column tiles.
