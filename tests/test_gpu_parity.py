@@ -348,3 +348,30 @@ def test_assemble_B_into_pinned_host_memory(lib, precision):
         lib.lrtei_assemble_B(pl.plan, 0, pageable, nb2)
     assert ei.value.status == 1
     pl.close()
+
+
+@pytest.mark.parametrize("precision", ["split_f16", "split_f16_8", "bf16"])
+@pytest.mark.parametrize("nshell", [1, 2])
+def test_tensor_core_paths_on_one_and_few_functions(lib, precision, nshell):
+    """Degenerate sizes through the tensor-core GEMMs: one s function (one unique pair, a 1 x 1
+    B_u inside a 128 x 128 tile) and an s plus a p shell (N_b = 4); B and a J-build against the
+    oracle within the precision's bound."""
+    import torch
+    shells = [synth.Shell(center=np.array([0.1, -0.2, 0.3]), l=0, exps=np.array([3.0, 0.4]),
+                          coefs=np.array([0.6, 0.5]))]
+    if nshell == 2:
+        shells.append(synth.Shell(center=np.array([1.2, 0.4, -0.7]), l=1, exps=np.array([1.1]),
+                                  coefs=np.array([1.0])))
+    atoms = np.array([sh.center for sh in shells])
+    m = synth.Molecule(atoms=atoms, shells=shells, omega=0.5, n=12, P=16, name=f"tiny{nshell}")
+    o = oracle.Oracle.from_molecule(m)
+    ref = o.assemble_B()
+    pl = lib.Plan(m, precision)
+    B = pl.assemble_B().cpu().numpy()
+    pl.status()
+    tol = {"split_f16": 1e-7, "split_f16_8": 1e-8, "bf16": 1e-3}[precision]
+    assert rel_fro(B, ref) <= tol
+    D = synth.random_densities(3, m.nbf, 2)
+    J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+    assert rel_fro(J, o.jbuild_factored(D)) <= tol
+    pl.close()
