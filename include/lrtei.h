@@ -149,7 +149,11 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
 /* ---- J-build (Section 5, eq. coulapprox in the density form J = mat(B vec(D))) ----------
  * d_D: R symmetric N_b x N_b densities (FP64, row-major, consecutive); d_J: same shape.
  * J_r(mu, nu) = sum_{ka, la} B(mu nu, ka la) D_r(ka, la), through the factored form, never
- * forming B.  Uses the plan's precision for the two M-contractions. */
+ * forming B.  Uses the plan's precision for the two M-contractions.  When the resident operands
+ * (F_u, F_u^T and the dense n^3 x n^3 K, with their slices) would take more than half of the free
+ * device memory, F_u is instead built in blocks of unique pairs, twice per call, and the node sum
+ * runs as FP64 mode products (eq. ig1); LRTEI_JBUILD_BLOCK=<pairs> in the environment forces this
+ * streamed form with that block size. */
 lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream);
 
 /* ---- batched J-builds (many molecules of uneven size in one graph-captured launch) -------

@@ -903,11 +903,134 @@ static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double
   return finish_launch("jbuild (tensor cores)");
 }
 
+// J-builds for plans whose F_u (npair x n^3) or dense K (n^3 x n^3) would not fit in device
+// memory: F_u is built in blocks of rb unique pairs, twice (once for X = F_u^T D_u, once for
+// J_u = F_u Y), and the node sum Y = sum_p w_p (A_x^p (x) A_y^p (x) A_z^p) X runs as FP64 mode
+// products (eq. ig1) instead of the dense K.  Split plans run both F_u contractions of each block
+// on the tensor cores; the block partials of X are summed in FP64.
+static lrtei_status jbuild_streamed(lrtei_plan* plan, const double* d_D, int R, double* d_J, int64_t rb,
+                                    cudaStream_t st) {
+  const int nbf = plan->basis.nbf, n = plan->n, P = plan->P;
+  const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;
+  const double pref = plan->omega / sqrt(kPi);
+  const bool tc = is_split(plan);
+  rb = std::max<int64_t>(1, std::min(rb, npair));
+  const int64_t nblk = (npair + rb - 1) / rb;
+  Scratch sc(st);
+  double *Du, *Xt, *Yt, *t1, *t2, *Ju, *Fb;
+  LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&Xt, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Yt, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t1, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t2, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Ju, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&Fb, (size_t)rb * n3));
+  launch_pack_density(nbf, R, d_D, Du, st);
+  if (!tc) {
+    for (int64_t r0 = 0; r0 < npair; r0 += rb) {  // X = sum over blocks of D_b^T F_b
+      const int64_t nr = std::min(npair, r0 + rb) - r0;
+      launch_build_F<double>(plan->t, n, plan->d_S, r0, r0 + nr, Fb, n3, st);
+      ProfScope ps("gemm_fp64", st);
+      gemm_cuda_core<double>(true, false, R, n3, nr, 1.0, Du + r0 * R, R, Fb, n3, r0 == 0 ? 0.0 : 1.0, Xt, n3, st);
+    }
+    {
+      ProfScope ps("kron", st);
+      launch_kron_apply(n, P, plan->d_C, plan->d_w, Xt, Yt, R, t1, t2, st);
+    }
+    for (int64_t r0 = 0; r0 < npair; r0 += rb) {  // J_b = F_b Y
+      const int64_t nr = std::min(npair, r0 + rb) - r0;
+      launch_build_F<double>(plan->t, n, plan->d_S, r0, r0 + nr, Fb, n3, st);
+      ProfScope ps("gemm_fp64", st);
+      gemm_cuda_core<double>(false, true, nr, R, n3, 1.0, Fb, n3, Yt, n3, 0.0, Ju + r0 * R, R, st);
+    }
+    launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+    return finish_launch("jbuild (streamed)");
+  }
+  // tensor cores: X^T blocks (R x n^3) into per-block partials, summed once
+  double *FbT, *DbT, *Xparts, *part;
+  LRTEI_TRY(sc.get(&FbT, (size_t)rb * n3));
+  LRTEI_TRY(sc.get(&DbT, (size_t)R * rb));
+  LRTEI_TRY(sc.get(&Xparts, (size_t)nblk * R * n3));
+  // split-K partials of the largest GEMM of any block (full blocks and the last, shorter one)
+  const int64_t nlast = npair - (nblk - 1) * rb;
+  const int64_t part_n = std::max({(int64_t)splits_for(n3, rb) * n3, (int64_t)splits_for(n3, nlast) * n3,
+                                   (int64_t)splits_for(rb, n3) * rb, (int64_t)splits_for(nlast, n3) * nlast});
+  LRTEI_TRY(sc.get(&part, (size_t)part_n * R));
+  SplitMatrix FbTsp, Dbsp, Fbsp, Ysp;
+  LRTEI_TRY(scratch_split(sc, FbTsp, n3, rb, false, plan));
+  LRTEI_TRY(scratch_split(sc, Dbsp, R, rb, true, plan));
+  LRTEI_TRY(scratch_split(sc, Fbsp, rb, n3, false, plan));
+  LRTEI_TRY(scratch_split(sc, Ysp, R, n3, true, plan));
+  for (int64_t b = 0; b < nblk; ++b) {
+    const int64_t r0 = b * rb, nr = std::min(npair, r0 + rb) - r0;
+    launch_build_F<double>(plan->t, n, plan->d_S, r0, r0 + nr, Fb, n3, st);
+    launch_transpose(Fb, nr, n3, n3, FbT, nr, st);
+    launch_transpose(Du + r0 * R, nr, R, R, DbT, nr, st);
+    SplitMatrix A = FbTsp, Bm = Dbsp;  // K = nr for this block
+    A.kpad = Bm.kpad = kpad256(nr);
+    {
+      ProfScope ps("split", st);
+      launch_split_rows(FbT, n3, nr, nr, A, false, nslices(plan), st);
+      launch_split_rows(DbT, R, nr, nr, Bm, true, nslices(plan), st);
+    }
+    const int sb = splits_for(n3, nr);
+    LRTEI_TRY(tc_gemm(A, Bm, n3, R, 1.0, Xparts + b * R * n3, n3, true, false, sb, part, plan->d_status, st));
+  }
+  launch_reduce_splits(Xparts, (int)nblk, R * n3, R, n3, n3, Xt, n3, st);
+  {
+    ProfScope ps("kron", st);
+    launch_kron_apply(n, P, plan->d_C, plan->d_w, Xt, Yt, R, t1, t2, st);
+  }
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(Yt, R, n3, n3, Ysp, true, nslices(plan), st);
+  }
+  for (int64_t b = 0; b < nblk; ++b) {
+    const int64_t r0 = b * rb, nr = std::min(npair, r0 + rb) - r0;
+    launch_build_F<double>(plan->t, n, plan->d_S, r0, r0 + nr, Fb, n3, st);
+    SplitMatrix A = Fbsp;
+    A.rows = nr;
+    {
+      ProfScope ps("split", st);
+      launch_split_rows(Fb, nr, n3, n3, A, false, nslices(plan), st);
+    }
+    LRTEI_TRY(tc_gemm(A, Ysp, nr, R, 1.0, Ju + r0 * R, R, false, false, splits_for(nr, n3), part, plan->d_status, st));
+  }
+  launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+  return finish_launch("jbuild (streamed, tensor cores)");
+}
+
+// Streamed J-builds: forced by LRTEI_JBUILD_BLOCK=<pairs per block>, else chosen when the
+// resident operands of the one-pass J-build would take more than half of the free device memory.
+static int64_t jbuild_stream_block(const lrtei_plan* plan) {
+  const char* env = getenv("LRTEI_JBUILD_BLOCK");
+  if (env && *env) return std::max<int64_t>(1, atoll(env));
+  // operands already resident: the one-pass J-build needs nothing more
+  if (is_split(plan) ? (plan->have_FTsp && plan->have_Fsp && plan->have_Ksp) : plan->d_F != nullptr) return 0;
+  const int64_t npair = plan->t.npair, n3 = (int64_t)plan->n * plan->n * plan->n;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const double f = (double)npair * n3, k = (double)n3 * n3;
+  // split: F (FP64) + F^T (FP64, transient) + F^T and F slices + K (FP64) and its slices;
+  // FP64: F.  Already-built operands are counted as if they had to be built.
+  const double need = is_split(plan) ? f * (8 + 8 + 6 + 8) + k * (8 + 6) : f * 8;
+  if (need <= 0.5 * (double)free_b) return 0;
+  const double per_row = (double)n3 * (is_split(plan) ? 8 + 8 + 8 + 8 : 8);
+  int64_t rb = (int64_t)(0.15 * (double)free_b / per_row);
+  rb = std::max<int64_t>(128, rb / 128 * 128);
+  return std::min(rb, npair);
+}
+
 lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream) {
   if (!plan || !d_D || !d_J) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
   if (R <= 0) { set_error("R must be positive (got %d)", R); return LRTEI_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   ProfScope ps_all("jbuild", st);
+  const int64_t rb = jbuild_stream_block(plan);
+  if (rb > 0) return jbuild_streamed(plan, d_D, R, d_J, rb, st);
   if (is_split(plan)) return jbuild_tc(plan, d_D, R, d_J, st);
   const int nbf = plan->basis.nbf, n = plan->n, P = plan->P;
   const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n;

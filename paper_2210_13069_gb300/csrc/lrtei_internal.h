@@ -148,6 +148,9 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
                      int* d_status, cudaStream_t st);
 void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,
                       cudaStream_t st);
+// out[i][j] = sum_q part[q * stride + i * ld + j] for i < rows, j < cols.
+void launch_reduce_splits(const double* part, int splits, int64_t stride, int64_t rows, int64_t cols, int64_t ld,
+                          double* out, int64_t ldo, cudaStream_t st);
 inline int64_t kpad256(int64_t k) { return (k + 255) / 256 * 256; }
 
 // Read-only view of a plan's resident device tables (for entry points defined outside

@@ -375,3 +375,29 @@ def test_tensor_core_paths_on_one_and_few_functions(lib, precision, nshell):
     J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
     assert rel_fro(J, o.jbuild_factored(D)) <= tol
     pl.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_f16", "split_f16_8"])
+def test_streamed_jbuild_matches_one_pass(lib, precision, monkeypatch):
+    """The streamed J-build (F_u built in blocks of unique pairs, node sum by mode products) on
+    the ragged 45-function instance, with 200-pair blocks (a ragged last block) and with one
+    block: against the one-pass J-build and the oracle."""
+    import torch
+    m = mol_ragged()
+    o = oracle.Oracle.from_molecule(m)
+    D = synth.random_densities(21, m.nbf, 9)
+    ref = o.jbuild_factored(D)
+    tol = {"fp64": 1e-12, "split_f16": 1e-7, "split_f16_8": 1e-8}[precision]
+    pl = lib.Plan(m, precision)
+    Dt = torch.as_tensor(D, device="cuda")
+    J1 = pl.jbuild(Dt).cpu().numpy()
+    for block in ("200", "5000"):
+        monkeypatch.setenv("LRTEI_JBUILD_BLOCK", block)
+        J = pl.jbuild(Dt).cpu().numpy()
+        pl.status()
+        err = rel_fro(J, ref)
+        print(f"streamed J-build {precision}, blocks of {block} pairs: {err:.3e} (one pass {rel_fro(J1, ref):.3e})")
+        assert err <= tol
+        if precision == "fp64":
+            assert rel_fro(J, J1) <= 1e-13
+    pl.close()

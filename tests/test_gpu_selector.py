@@ -110,3 +110,51 @@ def test_selector_meets_target_and_gains_over_fixed(lib, trained, tmp_path):
     sel2 = S.Selector.load(p)
     assert np.array_equal(sel.predict_raw(X[:50]), sel2.predict_raw(X[:50]))
 
+
+
+def test_selector_on_a_600_function_molecule(lib, trained):
+    """A 40-atom, 600-function s/p/d molecule (cube side 12 (40/12)^(1/3) bohr, omega = 0.3), eight
+    densities, target 1e-6: the factored J-build at the selected (n, P) and at the fixed (32, 48),
+    both split-F16 on the tensor cores, against an FP64 J-build at a larger (n, P).  F_u does not
+    fit in device memory at these orders, so the J-builds stream it in blocks of unique pairs.
+    The selected (n, P) meets the target."""
+    import time
+    import torch
+    from paper_2210_13069_gb300 import selector as S, synth
+    sel, _, _ = trained
+    target, R = 1e-6, 8
+    m = synth.random_molecule(5000, natoms=40, cube=12.0 * (40 / 12) ** (1 / 3), omega=0.3, n=32, P=48,
+                              name="nb600_spd")
+    assert m.nbf == 600
+    amin, amax, lmax = S.molecule_features(m)
+    probe = lib.Plan(m, "fp64", n=8, P=8)
+    half = 0.5 * max(probe.info["box_hi"][d] - probe.info["box_lo"][d] for d in range(3))
+    probe.close()
+    n_sel, P_sel, fb = sel.select(m.omega, half, amin, amax, lmax, target)
+    assert not fb, "the 600-function molecule lies inside the trained feature ranges"
+    n_ref, P_ref = min(max(n_sel, 32) + 8, 72), max(P_sel, 48) + 16
+    D = torch.as_tensor(synth.random_densities(600, m.nbf, R), device="cuda")
+
+    def jbuild(prec, n, P):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl = lib.Plan(m, prec, n=n, P=P)
+        J = pl.jbuild(D)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        pl.status()
+        pl.close()
+        out = J.cpu().numpy()
+        del J
+        torch.cuda.empty_cache()
+        return out, dt
+
+    J_sel, t_sel = jbuild("split_f16", n_sel, P_sel)
+    J_fix, t_fix = jbuild("split_f16", 32, 48)
+    J_ref, t_ref = jbuild("fp64", n_ref, P_ref)
+    e_sel = float(np.linalg.norm(J_sel - J_ref) / np.linalg.norm(J_ref))
+    e_fix = float(np.linalg.norm(J_fix - J_ref) / np.linalg.norm(J_ref))
+    print(f"selector N_b=600 (omega 0.3, box half-width {half:.1f}): selected (n, P) = ({n_sel}, {P_sel}): error "
+          f"{e_sel:.2e}, plan + J-build {t_sel:.1f} s; fixed (32, 48): error {e_fix:.2e}, {t_fix:.1f} s; "
+          f"reference FP64 ({n_ref}, {P_ref}) {t_ref:.1f} s")
+    assert e_sel <= target
