@@ -335,6 +335,18 @@ def run_ours(args, world, rank, local):
                     "avg_launch_ms": avg_ms, "share_of_step": tot_ms / (ms_local * args.steps),
                     "split_products": k_slices,
                     "issued_frac": achieved * k_slices / peak}
+        if args.precision == "split_f16":
+            # operand bytes the tensor-core GEMMs load per step (128 x 128 tiles, seven 16-bit planes
+            # of 128 rows per 64-deep K step), per SM and clock, against the per-SM TMA delivery
+            # measured with the MMAs switched off (65-68 B/clk/SM, independent of the SM count)
+            tm = (npair + 127) // 128
+            kpad = (n3 + 255) // 256 * 256
+            tiles = tm * ((n3 + 127) // 128) + tm * (tm + 1) // 2
+            loaded = tiles * (kpad // 64) * 7 * 128 * 64 * 2
+            mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            bpc = loaded * args.steps / (tot_ms / 1e3) / 152 / (mhz * 1e6)
+            roofline["operand_delivery"] = {"achieved_B_per_clk_per_sm": bpc, "ceiling_B_per_clk_per_sm": 66.0,
+                                            "frac": bpc / 66.0, "bytes_per_step": loaded}
 
     # ---- J-builds/s (32 densities), same plan
     jb = None
