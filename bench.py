@@ -371,8 +371,9 @@ def run_ours(args, world, rank, local):
         del D, J
 
     # ---- end to end through the public API: host basis in, host B out.  The plan is created
-    # from the host arrays every step; B is written straight into pinned host memory by the
-    # library's last kernel, so the 8.4 GB device-to-host transfer is inside the step.
+    # from the host arrays every step; the library moves B into pinned host memory band by band
+    # (copy-engine transfers overlapped with the next band's GEMMs), so the 8.4 GB
+    # device-to-host transfer is inside the step.
     e2e = None
     if not args.no_e2e:
         del B
@@ -381,7 +382,7 @@ def run_ours(args, world, rank, local):
         centers, ls, nprim, exps, coefs = mol.packed()
         h2d = centers.nbytes + ls.nbytes + nprim.nbytes + exps.nbytes + coefs.nbytes
         times = []
-        for it in range(3):
+        for it in range(6):  # the first builds the tuning choices of every GEMM shape; minimum of the rest
             barrier(world)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -393,19 +394,23 @@ def run_ours(args, world, rank, local):
             if it > 0:
                 times.append(dt)
         dt = max_over_ranks(min(times), world, device="cuda")
-        # one more pass with a synchronisation between the parts, for the breakdown only
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p2 = lrtei.Plan(mol, args.precision)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        p2.assemble_B(args.form, out=hostB)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        p2.close()
+        # passes with a synchronisation between the parts, for the breakdown only (minimum of three)
+        t_plan, t_asm = [], []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = lrtei.Plan(mol, args.precision)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            p2.assemble_B(args.form, out=hostB)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            p2.close()
+            t_plan.append(t1 - t0)
+            t_asm.append(t2 - t1)
         e2e = {"value": world * entries_per_step / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(nb2 * nb2 * 8), "s_per_step": dt,
-               "breakdown_s": {"plan_create": t1 - t0, "assemble_B_into_pinned_host": t2 - t1},
+               "breakdown_s": {"plan_create": min(t_plan), "assemble_B_into_pinned_host": min(t_asm)},
                "path": "lrtei_plan_create from host arrays + lrtei_assemble_B into pinned host memory"}
         del hostB
         torch.cuda.empty_cache()

@@ -112,9 +112,13 @@ lrtei_status lrtei_plan_status(lrtei_plan* plan);
 /* ---- full tensor (Theorem 1; eq. tensors) ----------------------------------------------
  * Writes all N_b^2 x N_b^2 entries of B, FP64, row-major with leading dimension ld >= N_b^2,
  * into the caller's buffer d_B: device memory, or page-locked host memory (cudaHostAlloc /
- * cudaHostRegister), which the final expansion kernel then writes directly across the
- * host link.  Pageable host memory returns LRTEI_ERR_ARG.  `form` selects the Hadamard or the
- * factored form. */
+ * cudaHostRegister).  Pageable host memory returns LRTEI_ERR_ARG.  `form` selects the Hadamard
+ * or the factored form.  Into host memory, the tensor-core precisions compute B_u in bands of
+ * 128-row blocks of its upper triangle and move each band's completed rows of B to the host
+ * with copy-engine transfers on a second stream while the next band runs (the call returns with
+ * that work queued on `stream`; ~1 GiB of device staging; LRTEI_HOST_BANDS (default 16) and
+ * LRTEI_HOST_CHUNK_ROWS override the band count and the rows per transfer); the FP64 and FP32
+ * paths write host memory from their expansion kernel directly across the host link. */
 lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, int64_t ld, void* stream);
 
 /* Rows [row_begin, row_end) of the unique-pair matrix B_u (rows and columns are unique pairs

@@ -35,14 +35,64 @@ __global__ void k_build_F(int n, int64_t nrows, const int64_t* __restrict__ pair
   }
 }
 
+// The same F_u with the pair's rows staged: X_j = c_j S_x(j, .) in shared memory (zero padded to a
+// multiple of 8 columns), and each thread owning a column q = m2 n + m3 and eight consecutive m1,
+// so that a row j costs one multiply (S_y S_z) and eight FMAs for eight outputs instead of three
+// FP64 operations per output.  The sum over j runs in the same order as above.
+template <typename T>
+__global__ void __launch_bounds__(256) k_build_F_staged(int n, int64_t nrows, const int64_t* __restrict__ pair_row,
+                                                        const double* __restrict__ row_c, const double* __restrict__ S,
+                                                        int64_t r0, T* __restrict__ F, int64_t ldF) {
+  extern __shared__ double X[];  // [rows of the pair][n8]
+  const int64_t r = r0 + blockIdx.x;
+  const int64_t j0 = pair_row[r];
+  const int I = (int)(pair_row[r + 1] - j0);
+  const int n8 = (n + 7) / 8 * 8, nn = n * n;
+  const double* Sx = S;
+  const double* Sy = S + (size_t)nrows * n;
+  const double* Sz = S + 2 * (size_t)nrows * n;
+  for (int e = threadIdx.x; e < I * n8; e += blockDim.x) {
+    const int j = e / n8, m1 = e % n8;
+    X[e] = m1 < n ? row_c[j0 + j] * Sx[(size_t)(j0 + j) * n + m1] : 0.0;
+  }
+  __syncthreads();
+  T* out = F + (size_t)blockIdx.x * ldF;
+  const int items = nn * (n8 / 8);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int q = it % nn, g = it / nn;
+    const int m2 = q / n, m3 = q % n;
+    double acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+    for (int j = 0; j < I; ++j) {
+      const double y = Sy[(size_t)(j0 + j) * n + m2] * Sz[(size_t)(j0 + j) * n + m3];
+      const double2* xr = reinterpret_cast<const double2*>(X + j * n8 + g * 8);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double2 x2 = xr[i];
+        acc[2 * i] = fma(x2.x, y, acc[2 * i]);
+        acc[2 * i + 1] = fma(x2.y, y, acc[2 * i + 1]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (g * 8 + i < n) out[(size_t)(g * 8 + i) * nn + q] = (T)acc[i];
+  }
+}
+
 template <typename T>
 void launch_build_F(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, T* d_F, int64_t ldF,
                     cudaStream_t st) {
+  const size_t smem = sizeof(double) * (size_t)t.maxI * ((n + 7) / 8 * 8);
+  const bool staged = t.maxI > 0 && smem <= 48 * 1024;
   int64_t nr = r1 - r0;
   while (nr > 0) {
     int64_t chunk = nr > (1LL << 30) ? (1LL << 30) : nr;
     count_launch();
-    k_build_F<T><<<(unsigned)chunk, 256, 0, st>>>(n, t.nrows, t.pair_row, t.row_c, d_S, r0, d_F, ldF);
+    if (staged)
+      k_build_F_staged<T><<<(unsigned)chunk, 256, smem, st>>>(n, t.nrows, t.pair_row, t.row_c, d_S, r0, d_F, ldF);
+    else
+      k_build_F<T><<<(unsigned)chunk, 256, 0, st>>>(n, t.nrows, t.pair_row, t.row_c, d_S, r0, d_F, ldF);
     r0 += chunk;
     d_F += chunk * ldF;
     nr -= chunk;
@@ -212,6 +262,25 @@ void launch_expand_B(const PairTable& t, int nbf, const double* d_Bu, int64_t ld
                      int64_t ldB, cudaStream_t st) {
   count_launch();
   k_expand_B<<<(unsigned)t.npair, 256, 0, st>>>(nbf, d_Bu, ldu, scale, d_B, ldB, t.pair_mu, t.pair_nu);
+}
+
+// One block per row R = a N_b + b of B: out row R - R0 = B_u row pair(a, b) over the columns (ka, la).
+__global__ void k_expand_B_rows(int nbf, const double* __restrict__ Bu, int64_t ldu, int64_t R0, double* __restrict__ out,
+                                int64_t ldo) {
+  const int64_t R = R0 + blockIdx.x;
+  const int a = (int)(R / nbf), b = (int)(R % nbf);
+  const double* src = Bu + (size_t)pair_idx(nbf, a, b) * ldu;
+  double* dst = out + (size_t)blockIdx.x * ldo;
+  const int64_t nc = (int64_t)nbf * nbf;
+  for (int64_t col = threadIdx.x; col < nc; col += blockDim.x)
+    dst[col] = src[pair_idx(nbf, (int)(col / nbf), (int)(col % nbf))];
+}
+
+void launch_expand_B_rows(int nbf, const double* d_Bu, int64_t ldu, int64_t R0, int64_t R1, double* d_out, int64_t ldo,
+                          cudaStream_t st) {
+  if (R1 <= R0) return;
+  count_launch();
+  k_expand_B_rows<<<(unsigned)(R1 - R0), 256, 0, st>>>(nbf, d_Bu, ldu, R0, d_out, ldo);
 }
 
 // d_u[r][q] = D_q(mu, nu) * (mu == nu ? 1 : 2); D stored R x N_b x N_b.

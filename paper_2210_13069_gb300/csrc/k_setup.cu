@@ -7,6 +7,8 @@
 // Gaussian, clipped to the box: one warp per (row, dimension), one lane per quadrature point.
 #include <math.h>
 
+#include <algorithm>
+
 #include "lrtei_internal.h"
 
 namespace lrtei {
@@ -204,17 +206,22 @@ void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf
 // S_d(row, m) = int_{lo_d}^{hi_d} (x-A)^i (x-B)^k K_AB exp(-p (x-P)^2) T_m((x - c_d)/h_d) dx.
 // One warp per (row, d); lane q holds quadrature point q of every panel and accumulates
 // f(x_q) w_q T_m(u_q) for all m in registers; a shared-memory transpose then sums over lanes.
+// Items are (d, row) = dr / nrows, dr % nrows with dr = rep[item] (or dr = item without rep;
+// rep[item] < 0 marks an unused item); item's moments go to S[item * n + m].
 template <int NM>
 __global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const double* row_p, const double* row_P,
                                                  const double* row_K, const double* row_A, const double* row_B,
                                                  const int8_t* row_pa, const int8_t* row_pb, const double* lo3,
-                                                 const double* hi3, const double* gz, const double* gw, double* S) {
+                                                 const double* hi3, const double* gz, const double* gw,
+                                                 const int64_t* rep, int64_t nitems, double* S) {
   __shared__ double red[4][32][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t item = (int64_t)blockIdx.x * 4 + warp;  // (d, row) with row fastest
-  const bool active = item < 3 * nrows;
-  const int d = active ? (int)(item / nrows) : 0;
-  const int64_t row = active ? item % nrows : 0;
+  const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+  int64_t dr = item < nitems ? (rep ? rep[item] : item) : -1;
+  const bool active = dr >= 0;  // keys that no row holds have rep = -1
+  if (!active) dr = 0;
+  const int d = (int)(dr / nrows);
+  const int64_t row = dr % nrows;
   double acc[NM];
 #pragma unroll
   for (int m = 0; m < NM; ++m) acc[m] = 0.0;
@@ -261,22 +268,86 @@ __global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const dou
     __syncwarp();
     double s = 0.0;
     for (int l = 0; l < 32; ++l) s += red[warp][l][lane];
-    if (active && m0 + lane < n) S[((size_t)d * nrows + row) * n + m0 + lane] = s;
+    if (active && m0 + lane < n) S[(size_t)item * n + m0 + lane] = s;
     __syncwarp();
   }
 }
 
+// Moment key of every (d, row): S_d of a row depends only on its shell pair (s_mu <= s_nu), its
+// primitive pair (j1, j2), d and the powers (i, k) of mu and nu in d, so rows that agree in these
+// have identical moments.  key = off(s_mu, s_nu) + ((j1 K_nu + j2) 3 + d) (l_mu + 1)(l_nu + 1)
+// + i (l_nu + 1) + k; rep[key] receives one (d, row) = d nrows + row holding it (any of them: their
+// inputs are identical, so a racing store of another one is harmless).
+__global__ void k_moment_keys(const PairTable t, const int* __restrict__ bf_shell, const int* __restrict__ bf_pow,
+                              const int* __restrict__ shell_nprim, const int* __restrict__ shell_l,
+                              const int64_t* __restrict__ sp_off, int nshells, int* __restrict__ key,
+                              int64_t* __restrict__ rep) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < t.nrows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int r = t.row_pair[row];
+    const int mu = t.pair_mu[r], nu = t.pair_nu[r];
+    const int s1 = bf_shell[mu], s2 = bf_shell[nu];
+    const int Kn = shell_nprim[s2];
+    const int j = (int)(row - t.pair_row[r]);
+    const int lb = shell_l[s2] + 1, cmb = (shell_l[s1] + 1) * lb;
+    const int64_t tri = (int64_t)s1 * nshells - (int64_t)s1 * (s1 - 1) / 2 + (s2 - s1);
+    const int64_t base = sp_off[tri] + (int64_t)((j / Kn) * Kn + j % Kn) * 3 * cmb;
+    for (int d = 0; d < 3; ++d) {
+      const int64_t u = base + d * cmb + bf_pow[3 * mu + d] * lb + bf_pow[3 * nu + d];
+      key[d * t.nrows + row] = (int)u;
+      rep[u] = d * t.nrows + row;
+    }
+  }
+}
+
+// S[dr][m] = Su[key[dr]][m] for dr < 3 nrows.
+__global__ void k_gather_moments(int64_t count, int n, const int* __restrict__ key, const double* __restrict__ Su,
+                                 double* __restrict__ S) {
+  const int64_t total = count * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t dr = e / n;
+    S[e] = Su[(int64_t)key[dr] * n + (e - dr * n)];
+  }
+}
+
+void launch_moment_keys(const PairTable& t, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
+                        const int* d_shell_l, const int64_t* d_sp_off, int nshells, int* d_key, int64_t* d_rep,
+                        cudaStream_t st) {
+  if (t.nrows <= 0) return;
+  count_launch();
+  const int64_t blocks = std::min<int64_t>((t.nrows + 255) / 256, 152 * 16);
+  k_moment_keys<<<(unsigned)blocks, 256, 0, st>>>(t, d_bf_shell, d_bf_pow, d_shell_nprim, d_shell_l, d_sp_off, nshells,
+                                                  d_key, d_rep);
+}
+
+void launch_gather_moments(int64_t count, int n, const int* d_key, const double* d_Su, double* d_S, cudaStream_t st) {
+  if (count <= 0) return;
+  count_launch();
+  const int64_t blocks = std::min<int64_t>((count * n + 255) / 256, 152 * 16);
+  k_gather_moments<<<(unsigned)blocks, 256, 0, st>>>(count, n, d_key, d_Su, d_S);
+}
+
 void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const double* d_gz,
-                    const double* d_gw, double* d_S, cudaStream_t st) {
-  const int64_t items = 3 * t.nrows;
+                    const double* d_gw, const int64_t* d_rep, int64_t nitems, double* d_S, cudaStream_t st) {
+  if (nitems <= 0) return;
+  const int64_t items = nitems;
   const unsigned blocks = (unsigned)((items + 3) / 4);
   count_launch();
-  if (n <= 32)
-    k_moments<32><<<blocks, 128, 0, st>>>(t.nrows, n, t.row_p, t.row_P, t.row_K, t.row_A, t.row_B, t.row_pa,
-                                          t.row_pb, d_lo3, d_hi3, d_gz, d_gw, d_S);
-  else
-    k_moments<64><<<blocks, 128, 0, st>>>(t.nrows, n, t.row_p, t.row_P, t.row_K, t.row_A, t.row_B, t.row_pa,
-                                          t.row_pb, d_lo3, d_hi3, d_gz, d_gw, d_S);
+  // accumulators for n rounded up to a multiple of 8 (the recurrence costs two FMAs per term)
+#define LRTEI_MOMENTS(NM)                                                                                       \
+  k_moments<NM><<<blocks, 128, 0, st>>>(t.nrows, n, t.row_p, t.row_P, t.row_K, t.row_A, t.row_B, t.row_pa, t.row_pb, \
+                                        d_lo3, d_hi3, d_gz, d_gw, d_rep, nitems, d_S)
+  switch ((n + 7) / 8) {
+    case 1: LRTEI_MOMENTS(8); break;
+    case 2: LRTEI_MOMENTS(16); break;
+    case 3: LRTEI_MOMENTS(24); break;
+    case 4: LRTEI_MOMENTS(32); break;
+    case 5: LRTEI_MOMENTS(40); break;
+    case 6: LRTEI_MOMENTS(48); break;
+    case 7: LRTEI_MOMENTS(56); break;
+    default: LRTEI_MOMENTS(64); break;
+  }
+#undef LRTEI_MOMENTS
 }
 
 }  // namespace lrtei

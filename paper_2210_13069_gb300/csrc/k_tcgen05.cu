@@ -81,6 +81,8 @@ struct Params {
   int symmetric;
   int splits;
   int* status;
+  int64_t a_row0;         // row of C that row 0 of A computes (a row band of a symmetric product)
+  int64_t blk0, blk1;     // symmetric product: the 128-row blocks [blk0, blk1) of the upper triangle
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -297,8 +299,8 @@ __device__ __forceinline__ Work work_item(const Params& p, int64_t item) {
     int64_t t = tile / SUB;
     const int sub = (int)(tile % SUB);
     int64_t r = 0, c = 0;
-    for (int64_t R0 = 0; R0 < nb; R0 += kGroupRows) {
-      const int64_t R1 = min(nb, R0 + kGroupRows), g = R1 - R0;
+    for (int64_t R0 = p.blk0; R0 < p.blk1; R0 += kGroupRows) {
+      const int64_t R1 = min(p.blk1, R0 + kGroupRows), g = R1 - R0;
       const int64_t in_group = g * (g + 1) / 2 + (nb - R1) * g;
       if (t >= in_group) { t -= in_group; continue; }
       for (c = R0; c < nb; ++c) {
@@ -411,16 +413,17 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
           mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
           uint8_t* st = smem + (size_t)s * STAGE_BYTES;
           const int kx = (w.c_begin * KSTEPS + kk) * BK;
+          const int ay = (int)(w.m0 - p.a_row0);
           uint8_t* sb = st + NA_ * A_BYTES;
-          tma_load_2d(&ta0, st + 0 * A_BYTES, &full[s], kx, (int)w.m0);
+          tma_load_2d(&ta0, st + 0 * A_BYTES, &full[s], kx, ay);
           tma_load_2d(&tb0, sb + 0 * B_BYTES, &full[s], kx, (int)w.n0);
           if constexpr (!PLAIN) {
-            tma_load_2d(&ta1, st + 1 * A_BYTES, &full[s], kx, (int)w.m0);
-            tma_load_2d(&ta2, st + 2 * A_BYTES, &full[s], kx, (int)w.m0);
+            tma_load_2d(&ta1, st + 1 * A_BYTES, &full[s], kx, ay);
+            tma_load_2d(&ta2, st + 2 * A_BYTES, &full[s], kx, ay);
             tma_load_2d(&tb1, sb + 1 * B_BYTES, &full[s], kx, (int)w.n0);
             tma_load_2d(&tb1h, sb + 2 * B_BYTES, &full[s], kx, (int)w.n0);
             tma_load_2d(&tb2, sb + 3 * B_BYTES, &full[s], kx, (int)w.n0);
-            if constexpr (P8) tma_load_2d(&ta1h, st + 3 * A_BYTES, &full[s], kx, (int)w.m0);
+            if constexpr (P8) tma_load_2d(&ta1h, st + 3 * A_BYTES, &full[s], kx, ay);
           }
         }
       }
@@ -568,7 +571,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
         st12[row * LDS + col0 + j] = T12[j];
         if constexpr (P8) st2[row * LDS + col0 + j] = T2[j];
       }
-      if (et < BM) sea[et] = (w.m0 + et < p.M) ? p.ea[w.m0 + et] : 0;
+      if (et < BM) sea[et] = (w.m0 + et < p.M) ? p.ea[w.m0 - p.a_row0 + et] : 0;
       if (et < BN) seb[et] = (w.n0 + et < p.N) ? p.eb[w.n0 + et] : 0;
       asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
       double* Cs = p.C + (int64_t)w.split * p.split_stride;
@@ -936,7 +939,8 @@ static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const 
     ProfScope ps("tc_gemm", st);
     return launch_cfg(A, B, p, splits, plain, cands[(i < 0 || i >= ncand) ? 0 : i], st);
   }
-  const auto key = std::make_tuple(p.M, p.N, A.kpad, splits, (int)plain + 2 * (int)A.eight, p.symmetric, p.transpose_out);
+  const auto key = std::make_tuple(p.M, p.N, A.kpad, splits, (int)plain + 2 * (int)A.eight,
+                                   p.symmetric ? (int)(1 + p.blk0) : 0, p.transpose_out);
   int choice = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -976,9 +980,9 @@ static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const 
 // C = scale * A B^T.  A: M rows (slices s0,s1,s2), B: N rows (slices s0,s1,s1h,s2), same kpad
 // (multiple of 256, <= 32768 per split).  d_C: FP64, ldc; transpose_out writes C^T.
 // When splits > 1, d_part (splits * M * N doubles) receives the partials, which are reduced into d_C.
-lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int64_t N, double scale, double* d_C,
-                     int64_t ldc, bool transpose_out, bool symmetric_upper, int splits, double* d_part,
-                     int* d_status, cudaStream_t st) {
+static lrtei_status tc_gemm_impl(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int64_t N, double scale,
+                                 double* d_C, int64_t ldc, bool transpose_out, bool symmetric_upper, int splits,
+                                 double* d_part, int* d_status, cudaStream_t st, int64_t row0) {
   if (A.kpad != B.kpad || A.kpad % tc::KCHUNK != 0) {
     set_error("tc_gemm: operands must share a K padded to a multiple of %d", tc::KCHUNK);
     return LRTEI_ERR_ARG;
@@ -991,8 +995,9 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
     return LRTEI_ERR_UNSUPPORTED;
   }
   splits = (nchunks + cps - 1) / cps;
-  if (symmetric_upper && (splits != 1 || M != N || transpose_out)) {
-    set_error("tc_gemm: symmetric mode needs one split and a square output");
+  if (symmetric_upper && (splits != 1 || M > N || transpose_out || row0 % tc::BM != 0 || row0 >= M ||
+                          A.rows < M - row0)) {
+    set_error("tc_gemm: symmetric mode needs one split and a square output (or a 128-aligned row band)");
     return LRTEI_ERR_ARG;
   }
   tc::Params p{};
@@ -1007,6 +1012,7 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
   p.symmetric = symmetric_upper ? 1 : 0;
   p.status = d_status;
   p.splits = splits;
+  p.a_row0 = row0;
   // Tile width: the tensor pipe runs at full rate from N = 128 on (a 128 x 64 MMA is bound by
   // its operand reads from shared memory); narrow outputs take narrower tiles.  Plain BF16 keeps
   // 64-column tiles.
@@ -1016,8 +1022,12 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
   p.tiles_m = tiles_m;
   p.tiles_n = tiles_n;
   if (symmetric_upper) {
-    // upper-triangular enumeration in units of 128 x 128 blocks, each done as 128 / BN tiles
-    p.ntiles = tiles_m * (tiles_m + 1) / 2 * (tc::BM / BN);
+    // upper-triangular enumeration in units of 128 x 128 blocks, each done as 128 / BN tiles;
+    // block rows [row0 / 128, ceil(M / 128)) of the nb x nb block triangle
+    const int64_t nb = (N + tc::BM - 1) / tc::BM;
+    p.blk0 = row0 / tc::BM;
+    p.blk1 = tiles_m;
+    p.ntiles = ((nb - p.blk0) * (nb - p.blk0 + 1) / 2 - (nb - p.blk1) * (nb - p.blk1 + 1) / 2) * (tc::BM / BN);
   } else {
     p.ntiles = tiles_m * tiles_n;
   }
@@ -1054,6 +1064,27 @@ lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int6
     if (e != cudaSuccess) return cuda_fail(e, "reduce_splits");
   }
   return LRTEI_OK;
+}
+
+lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int64_t N, double scale, double* d_C,
+                     int64_t ldc, bool transpose_out, bool symmetric_upper, int splits, double* d_part,
+                     int* d_status, cudaStream_t st) {
+  if (symmetric_upper && M != N) {
+    set_error("tc_gemm: symmetric mode needs a square output");
+    return LRTEI_ERR_ARG;
+  }
+  return tc_gemm_impl(A, B, M, N, scale, d_C, ldc, transpose_out, symmetric_upper, splits, d_part, d_status, st, 0);
+}
+
+lrtei_status tc_gemm_sym_band(const SplitMatrix& A, const SplitMatrix& B, int64_t row0, int64_t row1, int64_t N,
+                              double* d_C, int64_t ldc, int* d_status, cudaStream_t st) {
+  if (row0 == 0 && row1 == N) return tc_gemm_impl(A, B, N, N, 1.0, d_C, ldc, false, true, 1, nullptr, d_status, st, 0);
+  if (row0 % tc::BM != 0 || row0 >= row1 || row1 > N || (row1 < N && row1 % tc::BM != 0)) {
+    set_error("tc_gemm_sym_band: rows [%lld, %lld) are not a 128-aligned band of %lld", (long long)row0,
+              (long long)row1, (long long)N);
+    return LRTEI_ERR_ARG;
+  }
+  return tc_gemm_impl(A, B, row1, N, 1.0, d_C, ldc, false, true, 1, nullptr, d_status, st, row0);
 }
 
 }  // namespace lrtei

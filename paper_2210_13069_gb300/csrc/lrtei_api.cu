@@ -239,6 +239,7 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
       pmu[r] = mu;
       pnu[r] = nu;
       pI[r] = b.nprim[b.bf_shell[mu]] * b.nprim[b.bf_shell[nu]];
+      t.maxI = std::max(t.maxI, pI[r]);
       prow[r] = rows;
       rows += pI[r];
       ++r;
@@ -317,9 +318,51 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   launch_nodes_map(P, omega, pl->d_z, pl->d_s, st);
   launch_gauss_legendre(kMomentPts, pl->d_gz, pl->d_gw, st);
   launch_cheb_coeff(n, P, pl->d_s, pl->d_half3, pl->d_C, st);
+  // Moments of the distinct keys (shell pair, primitive pair, d, powers in d) only, gathered into
+  // the rows afterwards: rows that share a key have identical inputs, so S is the same as computed
+  // row by row (about half the work for an s/p/d basis).
   {
-    ProfScope ps("moments", st);
-    launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_gz, pl->d_gw, pl->d_S, st);
+    const int ns = b.nshells;
+    std::vector<int64_t> sp_off((size_t)ns * (ns + 1) / 2);
+    int64_t nkeys = 0;
+    for (int s1 = 0, k = 0; s1 < ns; ++s1)
+      for (int s2 = s1; s2 < ns; ++s2, ++k) {
+        sp_off[k] = nkeys;
+        nkeys += (int64_t)b.nprim[s1] * b.nprim[s2] * 3 * (b.l[s1] + 1) * (b.l[s2] + 1);
+      }
+    if (nkeys >= (int64_t)INT32_MAX) {  // keys are 32-bit: compute every row's moments directly
+      ProfScope ps("moments", st);
+      launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_gz, pl->d_gw, nullptr, 3 * t.nrows, pl->d_S, st);
+    } else {
+      int* d_key = nullptr;
+      int* d_l = nullptr;
+      int64_t *d_rep = nullptr, *d_off = nullptr;
+      double* d_Su = nullptr;
+      auto fin = [&](cudaError_t e, const char* what) {
+        for (void* q : {(void*)d_key, (void*)d_l, (void*)d_rep, (void*)d_off, (void*)d_Su})
+          if (q) cudaFreeAsync(q, st);
+        if (e != cudaSuccess) { delete pl; return cuda_fail(e, what); }
+        return LRTEI_OK;
+      };
+      if ((ce = cudaMallocAsync((void**)&d_key, sizeof(int) * 3 * (size_t)t.nrows, st)) != cudaSuccess ||
+          (ce = cudaMallocAsync((void**)&d_l, sizeof(int) * (size_t)ns, st)) != cudaSuccess ||
+          (ce = cudaMallocAsync((void**)&d_rep, sizeof(int64_t) * (size_t)nkeys, st)) != cudaSuccess ||
+          (ce = cudaMallocAsync((void**)&d_off, sizeof(int64_t) * sp_off.size(), st)) != cudaSuccess ||
+          (ce = cudaMallocAsync((void**)&d_Su, sizeof(double) * (size_t)nkeys * n, st)) != cudaSuccess)
+        return fin(ce, "moment key scratch");
+      if ((ce = cudaMemcpyAsync(d_l, b.l.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+          (ce = cudaMemcpyAsync(d_off, sp_off.data(), sizeof(int64_t) * sp_off.size(), cudaMemcpyHostToDevice, st)) !=
+              cudaSuccess ||
+          (ce = cudaMemsetAsync(d_rep, 0xFF, sizeof(int64_t) * (size_t)nkeys, st)) != cudaSuccess)
+        return fin(ce, "moment key upload");
+      launch_moment_keys(t, pl->d_bf_shell, pl->d_bf_pow, pl->d_shell_nprim, d_l, d_off, ns, d_key, d_rep, st);
+      {
+        ProfScope ps("moments", st);
+        launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_gz, pl->d_gw, d_rep, nkeys, d_Su, st);
+      }
+      launch_gather_moments(3 * t.nrows, n, d_key, d_Su, pl->d_S, st);
+      if ((s = fin(cudaGetLastError(), "moment kernels")) != LRTEI_OK) return s;
+    }
   }
   if ((s = finish_launch("plan set-up kernels")) != LRTEI_OK) { delete pl; return s; }
   *out = pl;
@@ -594,6 +637,117 @@ lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int
   return tc_gemm(Gs, pl->Fsp, nr, npair, 1.0, out, ld, false, sym, 1, nullptr, pl->d_status, st);
 }
 
+// Positive integer from the environment (0 when unset): the host-output pipeline's band count
+// and copy chunk, for tests that need many bands on a small molecule.
+static int64_t env_count(const char* name) {
+  const char* v = getenv(name);
+  return (v && *v) ? std::max<long long>(0, atoll(v)) : 0;
+}
+
+// B into page-locked host memory through the tensor-core path.  B_u is computed in bands of
+// 128-row blocks of its upper triangle (G_b = F_u,b K, then the band's blocks of G_b F_u^T, each
+// written with its mirror), so that after band b every B_u row below the band's end is complete.
+// The rows a N_b + b of B whose pairs are all complete (every a with pair(a, N_b - 1) done) are
+// expanded into one of two device staging slots and copied to the host by a copy engine on a
+// second stream, while the next band runs on the tensor cores.  Bands have equal GEMM work: block
+// row i costs ~ n^3 (its rows of G) + npair - 128 i (its part of the triangle).
+static lrtei_status assemble_B_host_banded(lrtei_plan* pl, double* hB, int64_t ld, cudaStream_t st) {
+  const int nbf = pl->basis.nbf;
+  const int64_t nb2 = (int64_t)nbf * nbf, npair = pl->t.npair, n3 = (int64_t)pl->n * pl->n * pl->n;
+  LRTEI_TRY(ensure_Fsp(pl, st, true));
+  LRTEI_TRY(ensure_Ksp(pl, st, true));
+  const int64_t nblk = (npair + 127) / 128;
+  int64_t nbands = env_count("LRTEI_HOST_BANDS");
+  if (nbands <= 0) nbands = 16;
+  nbands = std::min(nbands, nblk);
+  std::vector<int64_t> edge{0};  // band edges in 128-row blocks
+  {
+    double total = 0.0, acc = 0.0;
+    for (int64_t i = 0; i < nblk; ++i) total += (double)(n3 + npair - 128 * i);
+    for (int64_t i = 0; i < nblk; ++i) {
+      acc += (double)(n3 + npair - 128 * i);
+      if (acc >= total * (double)edge.size() / (double)nbands && i + 1 < nblk) edge.push_back(i + 1);
+    }
+    edge.push_back(nblk);
+  }
+  int64_t maxrows = 0;
+  for (size_t k = 0; k + 1 < edge.size(); ++k)
+    maxrows = std::max(maxrows, std::min(npair, 128 * edge[k + 1]) - 128 * edge[k]);
+  int64_t chunk = env_count("LRTEI_HOST_CHUNK_ROWS");
+  if (chunk <= 0) chunk = std::max<int64_t>(1, (int64_t)((512ULL << 20) / (sizeof(double) * (size_t)nb2)));
+  chunk = std::min(chunk, nb2);
+  Scratch sc(st);
+  double *Bu, *G, *stage[2];
+  LRTEI_TRY(sc.get(&Bu, (size_t)npair * npair));
+  LRTEI_TRY(sc.get(&G, (size_t)maxrows * n3));
+  LRTEI_TRY(sc.get(&stage[0], (size_t)chunk * nb2));
+  LRTEI_TRY(sc.get(&stage[1], (size_t)chunk * nb2));
+  SplitMatrix Gs;
+  LRTEI_TRY(scratch_split(sc, Gs, maxrows, n3, false, pl));
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ready[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr}, fin = nullptr;
+  lrtei_status status = LRTEI_OK;
+  auto fail = [&](cudaError_t e, const char* what) { if (status == LRTEI_OK) status = cuda_fail(e, what); };
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "copy stream");
+  for (int i = 0; i < 2 && status == LRTEI_OK; ++i) {
+    if ((e = cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming)) != cudaSuccess) fail(e, "event");
+    else if ((e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming)) != cudaSuccess) fail(e, "event");
+  }
+  if (status == LRTEI_OK && (e = cudaEventCreateWithFlags(&fin, cudaEventDisableTiming)) != cudaSuccess) fail(e, "event");
+  int64_t a_done = 0, nchunk = 0;
+  for (size_t k = 0; k + 1 < edge.size() && status == LRTEI_OK; ++k) {
+    const int64_t r0 = 128 * edge[k], r1 = std::min(npair, 128 * edge[k + 1]), nr = r1 - r0;
+    SplitMatrix Fr = pl->Fsp;  // row view [r0, r1)
+    Fr.rows = nr;
+    Fr.s0 += r0 * Fr.kpad;
+    if (Fr.s1h) Fr.s1h += r0 * Fr.kpad;
+    if (Fr.s1) Fr.s1 += r0 * Fr.kpad;
+    if (Fr.s2) Fr.s2 += r0 * Fr.kpad;
+    Fr.expo += r0;
+    if ((status = tc_gemm(Fr, pl->Ksp, nr, n3, 1.0, G, n3, false, false, 1, nullptr, pl->d_status, st)) != LRTEI_OK) break;
+    Gs.rows = nr;
+    {
+      ProfScope ps("split", st);
+      launch_split_rows(G, nr, n3, n3, Gs, false, nslices(pl), st);
+    }
+    if ((status = tc_gemm_sym_band(Gs, pl->Fsp, r0, r1, npair, Bu, npair, pl->d_status, st)) != LRTEI_OK) break;
+    // basis functions a whose pairs (a, b >= a) all lie below r1: rows [a_done N_b, a_end N_b) of B
+    int64_t a_end = a_done;
+    while (a_end < nbf && a_end * nbf - a_end * (a_end - 1) / 2 + (nbf - 1 - a_end) < r1) ++a_end;
+    for (int64_t R = a_done * nbf; R < a_end * nbf && status == LRTEI_OK; R += chunk, ++nchunk) {
+      const int64_t Rn = std::min(a_end * nbf, R + chunk);
+      const int slot = (int)(nchunk & 1);
+      if (nchunk >= 2 && (e = cudaStreamWaitEvent(st, copied[slot], 0)) != cudaSuccess) { fail(e, "wait copy"); break; }
+      {
+        ProfScope ps("expand_B", st);
+        launch_expand_B_rows(nbf, Bu, npair, R, Rn, stage[slot], nb2, st);
+      }
+      if ((status = finish_launch("expand_B_rows")) != LRTEI_OK) break;
+      if ((e = cudaEventRecord(ready[slot], st)) != cudaSuccess) { fail(e, "record"); break; }
+      if ((e = cudaStreamWaitEvent(cs, ready[slot], 0)) != cudaSuccess) { fail(e, "wait expand"); break; }
+      if (ld == nb2)
+        e = cudaMemcpyAsync(hB + R * ld, stage[slot], sizeof(double) * (size_t)(Rn - R) * nb2, cudaMemcpyDeviceToHost, cs);
+      else
+        e = cudaMemcpy2DAsync(hB + R * ld, sizeof(double) * ld, stage[slot], sizeof(double) * nb2, sizeof(double) * nb2,
+                              (size_t)(Rn - R), cudaMemcpyDeviceToHost, cs);
+      if (e != cudaSuccess) { fail(e, "copy B rows to host"); break; }
+      if ((e = cudaEventRecord(copied[slot], cs)) != cudaSuccess) { fail(e, "record"); break; }
+    }
+    a_done = a_end;
+  }
+  // the caller's stream (and the scratch frees queued on it) wait for the last copy
+  if (fin && cudaEventRecord(fin, cs) == cudaSuccess) cudaStreamWaitEvent(st, fin, 0);
+  else cudaStreamSynchronize(cs);
+  for (int i = 0; i < 2; ++i) {
+    if (ready[i]) cudaEventDestroy(ready[i]);
+    if (copied[i]) cudaEventDestroy(copied[i]);
+  }
+  if (fin) cudaEventDestroy(fin);
+  cudaStreamDestroy(cs);
+  return status;  // the last band ends at npair, so every row of B has been written
+}
+
 int choose_form(const lrtei_plan* pl, lrtei_form form) {
   if (is_split(pl)) return LRTEI_FORM_FACTORED;  // the tensor-core path runs the factored form
   if (form == LRTEI_FORM_HADAMARD || form == LRTEI_FORM_FACTORED) return form;
@@ -790,12 +944,14 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
   // The output may be device memory or page-locked host memory; in the latter case the
   // expansion kernel stores B through the buffer's device alias, so the device-to-host
   // transfer is the kernel's own write stream (no staging copy of B in device memory).
+  double* hB = nullptr;
   {
     cudaPointerAttributes pa{};
     cudaError_t e = cudaPointerGetAttributes(&pa, d_B);
     if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(B)");
     if (pa.type == cudaMemoryTypeHost) {
       if (!pa.devicePointer) { set_error("pinned host B is not mapped into the device address space"); return LRTEI_ERR_ARG; }
+      hB = d_B;
       d_B = static_cast<double*>(pa.devicePointer);
     } else if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) {
       set_error("B must be device memory or page-locked (pinned) host memory");
@@ -805,6 +961,7 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
   cudaStream_t st = (cudaStream_t)stream;
   const int f = choose_form(plan, form);
   plan->last_form = f;
+  if (hB && is_split(plan)) return assemble_B_host_banded(plan, hB, ld, st);
   // process B_u in row blocks of at most ~1 GiB
   int64_t rb = std::max<int64_t>(1, (int64_t)((1ULL << 30) / (sizeof(double) * (size_t)npair)));
   if (f == LRTEI_FORM_FACTORED) {

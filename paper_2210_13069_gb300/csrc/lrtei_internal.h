@@ -48,6 +48,7 @@ struct ProfScope {
 // basis pairs mu <= nu, grouped by pair).
 struct PairTable {
   int64_t npair = 0, nrows = 0;
+  int maxI = 0;                // largest number of rows of one pair (host copy)
   int* pair_mu = nullptr;      // [npair]
   int* pair_nu = nullptr;      // [npair]
   int64_t* pair_row = nullptr; // [npair + 1] first row of each pair
@@ -80,8 +81,19 @@ void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf
                       const int* d_shell_poff, const double* d_shell_center, const double* d_exps,
                       const int* d_bf_coff, const double* d_ncoef, cudaStream_t st);
 // S[d][row][m] for m < n, FP64.  d_gz/d_gw: kMomentPts Gauss-Legendre rule on [-1,1].
+// Items (d, row) = rep[i] (d nrows + row; i < nitems; rep NULL: i itself, nitems = 3 nrows; rep[i] < 0:
+// skipped) -> d_S[i][m].
 void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const double* d_gz,
-                    const double* d_gw, double* d_S, cudaStream_t st);
+                    const double* d_gw, const int64_t* d_rep, int64_t nitems, double* d_S, cudaStream_t st);
+// Moment keys: rows that share shell pair, primitive pair, d and the powers in d share S_d.
+// key[d nrows + row] in [0, nkeys) with nkeys = sum over shell pairs s1 <= s2 of
+// K_s1 K_s2 3 (l_s1 + 1)(l_s2 + 1) (offsets sp_off, triangular in the shell pair); rep[key] = one
+// d nrows + row holding it (rep preset to -1).
+void launch_moment_keys(const PairTable& t, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
+                        const int* d_shell_l, const int64_t* d_sp_off, int nshells, int* d_key, int64_t* d_rep,
+                        cudaStream_t st);
+// S[dr][m] = Su[key[dr]][m] for dr < count.
+void launch_gather_moments(int64_t count, int n, const int* d_key, const double* d_Su, double* d_S, cudaStream_t st);
 
 // ---------------------------------------------------------------- Hadamard form (FP64)
 // T[d][p][row][b] = sum_a S[d][row][a] C[d][p][a][b]
@@ -110,6 +122,10 @@ void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const
 // Expand the unique-pair square B_u (npair x npair, ld) into full B (N_b^2 x N_b^2, ldB), times scale.
 void launch_expand_B(const PairTable& t, int nbf, const double* d_Bu, int64_t ldu, double scale, double* d_B,
                      int64_t ldB, cudaStream_t st);
+// Rows [R0, R1) of full B (R = a N_b + b) from complete rows of B_u: out row R - R0 (ldo) is
+// row pair(min(a, b), max(a, b)) of B_u gathered over the columns (ka, la).
+void launch_expand_B_rows(int nbf, const double* d_Bu, int64_t ldu, int64_t R0, int64_t R1, double* d_out, int64_t ldo,
+                          cudaStream_t st);
 // Densities -> unique-pair vectors: d_u[r][q] = D_q(mu,nu) * (mu == nu ? 1 : 2).
 void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStream_t st);
 // Unique-pair results -> full symmetric J: J_q(mu,nu) = J_q(nu,mu) = scale * Ju[r][q].
@@ -146,6 +162,12 @@ void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld,
 lrtei_status tc_gemm(const SplitMatrix& A, const SplitMatrix& B, int64_t M, int64_t N, double scale, double* d_C,
                      int64_t ldc, bool transpose_out, bool symmetric_upper, int splits, double* d_part,
                      int* d_status, cudaStream_t st);
+// Block rows [row0, row1) of the symmetric product C = A B^T (N x N): the upper-triangular
+// 128 x 128 blocks of those rows, computed and mirrored.  A holds rows [row0, row1) only; row0 is a
+// multiple of 128, as is row1 unless it is N.  Rows of C at or above row0 are complete once every
+// band up to this one has run.
+lrtei_status tc_gemm_sym_band(const SplitMatrix& A, const SplitMatrix& B, int64_t row0, int64_t row1, int64_t N,
+                              double* d_C, int64_t ldc, int* d_status, cudaStream_t st);
 void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,
                       cudaStream_t st);
 // out[i][j] = sum_q part[q * stride + i * ld + j] for i < rows, j < cols.

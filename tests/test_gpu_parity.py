@@ -268,8 +268,9 @@ def test_split_f16_jbuild(lib):
 
 def test_split_f16_full_size_180(lib):
     """Full-size 180-function instance: sampled rows of B (tensor-core row path and the full
-    symmetric assembly) against the oracle, the whole B against the FP64 GPU path (within 1e-12
-    of the oracle on sampled rows above), and a 32-density J-build against the FP64 GPU path."""
+    symmetric assembly) against the oracle, the banded assembly into pinned host memory against
+    the device one (bit for bit), the whole B against the FP64 GPU path (within 1e-12 of the
+    oracle on sampled rows above), and a 32-density J-build against the FP64 GPU path."""
     import torch
     m = synth.workload_spd()
     o = oracle.Oracle.from_molecule(m)
@@ -292,6 +293,15 @@ def test_split_f16_full_size_180(lib):
     e_full_rows = rel_fro(np.array(rows_full), refs)
     print(f"split_f16 180 functions, sampled rows: rel. Frobenius {e_rows:.3e} (row path), {e_full_rows:.3e} (assembly)")
     assert e_rows <= 1e-7 and e_full_rows <= 1e-7
+    # the same B into pinned host memory (16 bands, copy-engine transfers) is bit-identical
+    Bh = torch.empty((nbf * nbf, nbf * nbf), dtype=torch.float64, pin_memory=True)
+    pl.assemble_B(out=Bh)
+    torch.cuda.synchronize()
+    pl.status()
+    step = 2048
+    for i in range(0, nbf * nbf, step):
+        assert torch.equal(full[i:i + step].cpu(), Bh[i:i + step]), i
+    del Bh
     p64 = lib.Plan(m, "fp64")
     B64 = p64.assemble_B()
     e_all = float(torch.linalg.norm(full - B64) / torch.linalg.norm(B64))
@@ -327,11 +337,20 @@ def test_split_f16_each_tile_config(lib, cfg, monkeypatch):
         assert rel_fro(J, o.jbuild_factored(D)) <= 1e-7, R
 
 
-@pytest.mark.parametrize("precision", ["fp64", "split_f16", "split_f16_8"])
-def test_assemble_B_into_pinned_host_memory(lib, precision):
-    """B written by the device straight into pinned host memory equals B in device memory, bit
-    for bit; pageable host memory is refused before any launch."""
+@pytest.mark.parametrize("precision,bands,chunk", [
+    ("fp64", None, None), ("split_f16", None, None), ("split_f16_8", None, None), ("bf16", None, None),
+    ("split_f16", "1", None), ("split_f16", "3", "7"), ("split_f16_8", "4", "50")])
+def test_assemble_B_into_pinned_host_memory(lib, precision, bands, chunk, monkeypatch):
+    """B assembled into pinned host memory equals B in device memory, bit for bit: on the
+    tensor-core path through bands of the upper triangle (N_b = 45: 1035 unique pairs, nine
+    128-row blocks, so the default runs nine bands) with copy-engine transfers of the completed
+    rows, also as one band, and as three or four bands with ragged transfer chunks; also with a
+    leading dimension above N_b^2.  Pageable host memory is refused before any launch."""
     import torch
+    if bands:
+        monkeypatch.setenv("LRTEI_HOST_BANDS", bands)
+    if chunk:
+        monkeypatch.setenv("LRTEI_HOST_CHUNK_ROWS", chunk)
     m = mol_ragged()
     pl = lib.Plan(m, precision)
     Bd = pl.assemble_B().cpu()
@@ -341,6 +360,12 @@ def test_assemble_B_into_pinned_host_memory(lib, precision):
     torch.cuda.synchronize()
     pl.status()
     assert torch.equal(Bd, Bh)
+    wide = torch.full((nb2, nb2 + 3), float("nan"), dtype=torch.float64, pin_memory=True)
+    lib.lrtei_assemble_B(pl.plan, 0, wide, nb2 + 3)
+    torch.cuda.synchronize()
+    pl.status()
+    assert torch.equal(Bd, wide[:, :nb2])
+    assert torch.isnan(wide[:, nb2:]).all()
     pageable = torch.empty((nb2, nb2), dtype=torch.float64)
     with pytest.raises(ValueError):
         pl.assemble_B(out=pageable)
