@@ -157,7 +157,13 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
  * (F_u, F_u^T and the dense n^3 x n^3 K, with their slices) would take more than half of the free
  * device memory, F_u is instead built in blocks of unique pairs, twice per call, and the node sum
  * runs as FP64 mode products (eq. ig1); LRTEI_JBUILD_BLOCK=<pairs> in the environment forces this
- * streamed form with that block size. */
+ * streamed form with that block size.  A call repeating an earlier one-pass call's plan, d_D, d_J
+ * and R replays a CUDA graph of its kernels, captured after that call ran (the densities are read
+ * at replay time; up to 32 graphs are kept, least recently used dropped first, each holding its
+ * scratch memory; a plan's graphs are dropped when its operands are rebuilt or it is destroyed).
+ * Streamed calls, calls on a stream the caller is capturing, and LRTEI_JBUILD_GRAPH=0 launch
+ * kernel by kernel.  The environment switches are read when a call is made; a replayed graph
+ * keeps the choices of the call it was captured from. */
 lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream);
 
 /* ---- batched J-builds (many molecules of uneven size in one graph-captured launch) -------

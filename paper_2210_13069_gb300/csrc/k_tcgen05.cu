@@ -606,168 +606,6 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
   }
 }
 
-// ------------------------------------------------------------------ slicing
-__device__ __forceinline__ uint16_t f16_bits(float f) {
-  __half h = __float2half_rn(f);
-  return *reinterpret_cast<uint16_t*>(&h);
-}
-
-// round(x 2^(30 - e)) as an integer, from the bit pattern of x (no FP64 arithmetic: this
-// device's FP64 rate would make the slicing ALU-bound).  For |x| < 2^e 255/256 the result is
-// below 255 * 2^22 in magnitude; zeros and subnormals give 0.
-__device__ __forceinline__ int64_t fixed30(double x, int e) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FF);
-  if (E == 0) return 0;
-  const uint64_t m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);  // x = +-m 2^(E-1075)
-  const int sh = E - 1075 + 30 - e;
-  int64_t q;
-  if (sh >= 0)
-    q = (int64_t)(m << (sh > 11 ? 11 : sh));  // not reached for |x| < 2^e (then sh <= -22)
-  else if (sh < -62)
-    q = 0;
-  else
-    q = (int64_t)((m + (1ULL << (-sh - 1))) >> (-sh));  // round half up
-  return (b >> 63) ? -q : q;
-}
-
-// Slices of one element: q = round(x 2^(30-e)), s0 = round(q / 2^22), r = q - s0 2^22,
-// t1 = round(r / 2^11), t2 = r - t1 2^11; x ~ 2^e (s0 2^-8 + t1 2^-19 + t2 2^-30).
-// Stored as FP16: s0, t1, t2 / 2^11 and (optionally) t1 / 2^11 -- all exact.
-__device__ __forceinline__ void slice_store(double x, int e, bool live, int nslices, int64_t o, uint16_t* s0,
-                                            uint16_t* s1, uint16_t* s2, uint16_t* s1h) {
-  float a = 0.f, b = 0.f, c = 0.f;
-  if (live) {
-    const int64_t q = fixed30(x, e);
-    const int64_t q0 = (q + (1LL << 21)) >> 22;
-    const int64_t r = q - (q0 << 22);
-    const int64_t q1 = (r + (1LL << 10)) >> 11;
-    const int64_t q2 = r - (q1 << 11);
-    a = (float)q0;
-    b = nslices > 1 ? (float)q1 : 0.f;
-    c = nslices > 2 ? (float)q2 : 0.f;
-  }
-  s0[o] = f16_bits(a);
-  s1[o] = f16_bits(b);
-  s2[o] = f16_bits(c * (1.0f / 2048.0f));
-  if (s1h) s1h[o] = f16_bits(b * (1.0f / 2048.0f));
-}
-
-// Largest |x| of the row from the bit patterns (finite inputs order like their magnitudes),
-// then e with max|x| * 256/255 < 2^e (0 for an all-zero row).
-__device__ __forceinline__ int row_exponent(uint64_t mxbits, uint64_t* red, bool& nonzero) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t other = __shfl_xor_sync(0xffffffffu, mxbits, o);
-    mxbits = other > mxbits ? other : mxbits;
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mxbits;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint64_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ULL;
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t other = __shfl_xor_sync(0xffffffffu, v, o);
-      v = other > v ? other : v;
-    }
-    if (threadIdx.x == 0) red[0] = v;
-  }
-  __syncthreads();
-  const double mx = __longlong_as_double((long long)red[0]);
-  int e = 0;
-  if (mx > 0.0) frexp(mx * (256.0 / 255.0), &e);
-  nonzero = mx > 0.0 && e >= -1000;  // rows below ~1e-301 are treated as zero
-  return e;
-}
-
-// One block per row; rows of up to 1024 * EPT elements are read once and kept in registers.
-template <int EPT>
-__global__ void __launch_bounds__(1024) k_split_rows_reg(const double* __restrict__ src, int64_t rows, int64_t k, int64_t ld,
-                                                        int64_t kpad, uint16_t* __restrict__ s0, uint16_t* __restrict__ s1,
-                                                        uint16_t* __restrict__ s2, uint16_t* __restrict__ s1h,
-                                                        int* __restrict__ expo, int nslices) {
-  __shared__ uint64_t red[32];
-  const int64_t r = blockIdx.x;
-  const double* x = src + r * ld;
-  double v[EPT];
-  uint64_t mx = 0;
-#pragma unroll
-  for (int j = 0; j < EPT; ++j) {
-    const int64_t i = threadIdx.x + (int64_t)j * blockDim.x;
-    v[j] = i < k ? x[i] : 0.0;
-    const uint64_t a = (uint64_t)__double_as_longlong(v[j]) & 0x7FFFFFFFFFFFFFFFULL;
-    mx = a > mx ? a : mx;
-  }
-  bool nz;
-  const int e = row_exponent(mx, red, nz);
-  if (threadIdx.x == 0) expo[r] = e;
-#pragma unroll
-  for (int j = 0; j < EPT; ++j) {
-    const int64_t i = threadIdx.x + (int64_t)j * blockDim.x;
-    if (i < kpad) slice_store(v[j], e, i < k && nz, nslices, r * kpad + i, s0, s1, s2, s1h);
-  }
-  for (int64_t i = threadIdx.x + (int64_t)EPT * blockDim.x; i < kpad; i += blockDim.x)
-    slice_store(0.0, e, false, nslices, r * kpad + i, s0, s1, s2, s1h);
-}
-
-// Long rows: two passes over the row (maximum, then slices).
-__global__ void k_split_rows(const double* __restrict__ src, int64_t rows, int64_t k, int64_t ld, int64_t kpad,
-                             uint16_t* __restrict__ s0, uint16_t* __restrict__ s1, uint16_t* __restrict__ s2,
-                             uint16_t* __restrict__ s1h, int* __restrict__ expo, int nslices) {
-  __shared__ uint64_t red[32];
-  const int64_t r = blockIdx.x;
-  const double* x = src + r * ld;
-  uint64_t mx = 0;
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
-    const uint64_t a = (uint64_t)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFULL;
-    mx = a > mx ? a : mx;
-  }
-  bool nz;
-  const int e = row_exponent(mx, red, nz);
-  if (threadIdx.x == 0) expo[r] = e;
-  for (int64_t i = threadIdx.x; i < kpad; i += blockDim.x)
-    slice_store(i < k ? x[i] : 0.0, e, i < k && nz, nslices, r * kpad + i, s0, s1, s2, s1h);
-}
-
-// Plain BF16 operands: one rounded copy per element, exponent 8 so that the epilogue scale
-// 2^(ea + eb - 16) is 1.
-__global__ void k_plain_rows(const double* __restrict__ src, int64_t rows, int64_t k, int64_t ld, int64_t kpad,
-                             uint16_t* __restrict__ s0, int* __restrict__ expo) {
-  const int64_t r = blockIdx.x;
-  if (threadIdx.x == 0) expo[r] = 8;
-  for (int64_t i = threadIdx.x; i < kpad; i += blockDim.x) {
-    const float v = i < k ? (float)src[r * ld + i] : 0.f;
-    __nv_bfloat16 h = __float2bfloat16_rn(v);
-    s0[r * kpad + i] = *reinterpret_cast<uint16_t*>(&h);
-  }
-}
-
-// 32 x 32 tiled transpose of an FP64 matrix: out (cols x rows) = in (rows x cols)^T.
-__global__ void k_transpose(const double* __restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
-                            double* __restrict__ out, int64_t ldo) {
-  __shared__ double t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int64_t r = r0 + i, c = c0 + threadIdx.x;
-    if (r < rows && c < cols) t[i][threadIdx.x] = in[r * ldi + c];
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int64_t c = c0 + i, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) out[c * ldo + r] = t[threadIdx.x][i];
-  }
-}
-
-// Sum of split-K partials: out[i] = sum_s part[s * stride + i] (row-major rows x cols, ld).
-__global__ void k_reduce_splits(const double* __restrict__ part, int splits, int64_t stride, int64_t rows,
-                                int64_t cols, int64_t ld, double* __restrict__ out, int64_t ldo) {
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / cols, j = t % cols;
-    double s = 0.0;
-    for (int q = 0; q < splits; ++q) s += part[q * stride + i * ld + j];
-    out[i * ldo + j] = s;
-  }
-}
-
 // ------------------------------------------------------------------ host side
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -851,41 +689,6 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
 }
 
 }  // namespace tc
-
-void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld, SplitMatrix& m, bool with_s1h,
-                       int nslices, cudaStream_t st) {
-  if (rows <= 0) return;
-  count_launch();
-  if (m.plain) {
-    tc::k_plain_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.expo);
-    return;
-  }
-  uint16_t* s1h = (with_s1h || m.eight) ? m.s1h : nullptr;
-  if (k <= 1024 * 16)
-    tc::k_split_rows_reg<16><<<(unsigned)rows, 1024, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h,
-                                                             m.expo, nslices);
-  else
-    tc::k_split_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h, m.expo,
-                                                     nslices);
-}
-
-void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,
-                      cudaStream_t st) {
-  if (rows <= 0 || cols <= 0) return;
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
-  count_launch();
-  tc::k_transpose<<<grid, block, 0, st>>>(in, rows, cols, ldi, out, ldo);
-}
-
-void launch_reduce_splits(const double* part, int splits, int64_t stride, int64_t rows, int64_t cols, int64_t ld,
-                          double* out, int64_t ldo, cudaStream_t st) {
-  const int64_t total = rows * cols;
-  if (total <= 0) return;
-  int64_t b = (total + 255) / 256;
-  if (b > 152 * 32) b = 152 * 32;
-  count_launch();
-  tc::k_reduce_splits<<<(unsigned)b, 256, 0, st>>>(part, splits, stride, rows, cols, ld, out, ldo);
-}
 
 namespace tc {
 // Kernel configurations (BN, BK, stages) the tuner chooses from.

@@ -106,6 +106,7 @@ struct lrtei_plan {
 };
 
 static void forget_plan_graphs(const lrtei_plan* pl);
+static lrtei_status jbuild_direct(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st);
 
 #define LRTEI_TRY(expr)                    \
   do {                                     \
@@ -476,7 +477,11 @@ lrtei_status alloc_split(lrtei_plan* pl, SplitMatrix& m, int64_t rows, int64_t k
   return LRTEI_OK;
 }
 
+// Captured J-build graphs hold the plan's operand pointers: they are dropped before any of the
+// plan's buffers is freed (an operand rebuilt with another layout would otherwise be read
+// through its freed address by the next replay).
 void release_split(lrtei_plan* pl, SplitMatrix& m) {
+  forget_plan_graphs(pl);
   const size_t b = (size_t)m.rows * m.kpad * sizeof(uint16_t);
   pl->release(m.s0, b);
   pl->release(m.s1, b);
@@ -510,6 +515,7 @@ void drop_F64_if_sliced(lrtei_plan* pl, cudaStream_t st) {
   if (!is_split(pl) || !pl->d_F || !pl->have_Fsp || !pl->have_FTsp) return;
   cudaStreamSynchronize(st);  // the slicing kernels read d_F
   const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
+  forget_plan_graphs(pl);
   pl->release(pl->d_F, sizeof(double) * (size_t)pl->t.npair * n3);
   pl->d_F = nullptr;
 }
@@ -604,9 +610,19 @@ lrtei_status scratch_split(Scratch& sc, SplitMatrix& m, int64_t rows, int64_t k,
   return LRTEI_OK;
 }
 
+// Positive integer from the environment (0 when unset): the host-output pipeline's band count
+// and copy chunk, for tests that need many bands on a small molecule.
+static int64_t env_count(const char* name) {
+  const char* v = getenv(name);
+  return (v && *v) ? std::max<long long>(0, atoll(v)) : 0;
+}
+
+// Split-K count of a skinny tensor-core product (M rows, K deep); LRTEI_SPLITK overrides it.
 int splits_for(int64_t M, int64_t K) {
   const int64_t tiles = (M + 127) / 128;
   int64_t s = (kpad256(K) + 32767) / 32768;
+  const int64_t forced = env_count("LRTEI_SPLITK");
+  if (forced > 0) return (int)std::max(s, std::min<int64_t>(forced, kpad256(K) / 256));
   while (tiles * s < 2 * 152 && s * 256 * 2 <= kpad256(K)) s *= 2;
   return (int)s;
 }
@@ -635,13 +651,6 @@ lrtei_status bu_rows_tc(lrtei_plan* pl, int64_t r0, int64_t r1, double* out, int
   }
   const bool sym = (r0 == 0 && r1 == npair && ld == npair);
   return tc_gemm(Gs, pl->Fsp, nr, npair, 1.0, out, ld, false, sym, 1, nullptr, pl->d_status, st);
-}
-
-// Positive integer from the environment (0 when unset): the host-output pipeline's band count
-// and copy chunk, for tests that need many bands on a small molecule.
-static int64_t env_count(const char* name) {
-  const char* v = getenv(name);
-  return (v && *v) ? std::max<long long>(0, atoll(v)) : 0;
 }
 
 // B into page-locked host memory through the tensor-core path.  B_u is computed in bands of
@@ -816,9 +825,12 @@ constexpr int kSideStreams = 4;
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;
+  unsigned long long used = 0;  // last use (least recently used graphs are evicted)
 };
 std::mutex g_batch_mu;
 std::map<std::vector<uintptr_t>, BatchGraph> g_batch;
+unsigned long long g_batch_tick = 0;
+constexpr size_t kMaxGraphs = 32;  // each graph keeps its scratch memory reserved
 
 lrtei_status capture_batch(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,
                            double* const* d_J, cudaStream_t st, BatchGraph* out) {
@@ -836,7 +848,7 @@ lrtei_status capture_batch(lrtei_plan* const* plans, int nmol, const double* con
   cudaEventRecord(fork, origin);
   for (int i = 0; i < kSideStreams; ++i) cudaStreamWaitEvent(side[i], fork, 0);
   for (int m = 0; m < nmol && status == LRTEI_OK; ++m)
-    status = lrtei_jbuild(plans[m], d_D[m], R[m], d_J[m], side[m % kSideStreams]);
+    status = jbuild_direct(plans[m], d_D[m], R[m], d_J[m], side[m % kSideStreams]);
   for (int i = 0; i < kSideStreams; ++i) {
     cudaEventRecord(join[i], side[i]);
     cudaStreamWaitEvent(origin, join[i], 0);
@@ -888,6 +900,7 @@ lrtei_status batched_graph_run(lrtei_plan* const* plans, int nmol, const double*
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_batch.find(key);
     if (it != g_batch.end()) {
+      it->second.used = ++g_batch_tick;
       ProfScope ps("batched", st);
       LRTEI_CUDA(cudaGraphLaunch(it->second.exec, st));
       count_launches(it->second.kernels);
@@ -896,10 +909,18 @@ lrtei_status batched_graph_run(lrtei_plan* const* plans, int nmol, const double*
   }
   // First call for this set: run it directly (this also settles the GEMM tuning choices for
   // every shape), then capture the same work into a graph for the calls that follow.
-  for (int m = 0; m < nmol; ++m) LRTEI_TRY(lrtei_jbuild(plans[m], d_D[m], R[m], d_J[m], st));
+  for (int m = 0; m < nmol; ++m) LRTEI_TRY(jbuild_direct(plans[m], d_D[m], R[m], d_J[m], st));
   BatchGraph g;
   LRTEI_TRY(capture_batch(plans, nmol, d_D, R, d_J, st, &g));
   std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (g_batch.size() >= kMaxGraphs) {
+    auto old = g_batch.begin();
+    for (auto it = g_batch.begin(); it != g_batch.end(); ++it)
+      if (it->second.used < old->second.used) old = it;
+    cudaGraphExecDestroy(old->second.exec);
+    g_batch.erase(old);
+  }
+  g.used = ++g_batch_tick;
   g_batch[key] = g;
   return LRTEI_OK;
 }
@@ -1181,10 +1202,10 @@ static int64_t jbuild_stream_block(const lrtei_plan* plan) {
   return std::min(rb, npair);
 }
 
-lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream) {
-  if (!plan || !d_D || !d_J) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
-  if (R <= 0) { set_error("R must be positive (got %d)", R); return LRTEI_ERR_ARG; }
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+// One J-build launched kernel by kernel (also what a captured graph replays).
+static lrtei_status jbuild_direct(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st) {
   ProfScope ps_all("jbuild", st);
   const int64_t rb = jbuild_stream_block(plan);
   if (rb > 0) return jbuild_streamed(plan, d_D, R, d_J, rb, st);
@@ -1217,6 +1238,26 @@ lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_
   }
   launch_unpack_J(nbf, R, Ju, pref, d_J, st);
   return finish_launch("jbuild");
+}
+
+extern "C" {
+
+// Repeated J-builds with the same plan, densities, output and R replay a CUDA graph of the
+// kernel sequence (captured after the first such call has run directly); streamed J-builds, calls
+// on a stream the caller is capturing, and LRTEI_JBUILD_GRAPH=0 launch kernel by kernel.
+lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream) {
+  if (!plan || !d_D || !d_J) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (R <= 0) { set_error("R must be positive (got %d)", R); return LRTEI_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const char* g = getenv("LRTEI_JBUILD_GRAPH");
+  const bool graphs = !(g && g[0] == '0');
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (!graphs || jbuild_stream_block(plan) > 0 || cudaStreamIsCapturing(st, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return jbuild_direct(plan, d_D, R, d_J, st);
+  }
+  return batched_graph_run(&plan, 1, &d_D, &R, &d_J, st);
 }
 
 lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const double* const* d_D, const int* R,

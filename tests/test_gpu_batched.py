@@ -61,3 +61,32 @@ def test_batched_matches_single_and_oracle(lib, precision, tol):
     for p in plans:
         p.status()
         p.close()
+
+
+def test_batched_graph_after_operands_rebuilt(lib):
+    """A six-product plan keeps F_u and K without the fourth slice plane until a B assembly needs
+    it; the assembly rebuilds both, so a J-build graph captured before it is dropped and captured
+    again: the next batched call still equals single J-builds."""
+    import torch
+    mols = small_batch()[:3]
+    plans = [lib.Plan(m, "split_f16") for m in mols]
+    Rs = [4, 2, 5]
+    Ds = [torch.as_tensor(synth.random_densities(700 + i, m.nbf, Rs[i]), device="cuda") for i, m in enumerate(mols)]
+    Js = [torch.empty_like(D) for D in Ds]
+    for _ in range(2):  # run and capture, then replay
+        lib.lrtei_jbuild_batched([p.plan for p in plans], Ds, Rs, Js)
+    torch.cuda.synchronize()
+    first = [J.clone() for J in Js]
+    B = plans[0].assemble_B()  # rebuilds the slices of F_u and K with the t1 / 2^11 plane
+    for _ in range(2):
+        for J in Js:
+            J.fill_(float("nan"))
+        lib.lrtei_jbuild_batched([p.plan for p in plans], Ds, Rs, Js)
+        torch.cuda.synchronize()
+        for i in range(len(plans)):
+            assert torch.equal(Js[i], plans[i].jbuild(Ds[i])), i
+            assert rel(Js[i].cpu().numpy(), first[i].cpu().numpy()) <= 1e-12, i
+    del B
+    for p in plans:
+        p.status()
+        p.close()
