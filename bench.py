@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-nb360", action="store_true")
     ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
+    ap.add_argument("--profile-region", choices=["none", "main", "jbuild"], default="none",
+                    help="bracket that leg's timed launches with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="oracle seconds per step of the reference arm (default: the run stays within ~2.5 min)")
     return ap.parse_args()
@@ -276,10 +278,14 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
+    if args.profile_region == "main":
+        torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         plan.assemble_B(args.form, out=B)
     e1.record(stream)
+    if args.profile_region == "main":
+        torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
@@ -360,10 +366,14 @@ def run_ours(args, world, rank, local):
         j0 = torch.cuda.Event(enable_timing=True)
         j1 = torch.cuda.Event(enable_timing=True)
         reps = 3
+        if args.profile_region == "jbuild":
+            torch.cuda.profiler.start()
         j0.record(stream)
         for _ in range(reps):
             plan.jbuild(D, out=J)
         j1.record(stream)
+        if args.profile_region == "jbuild":
+            torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         jms = j0.elapsed_time(j1) / reps
         jb = {"value": world * R / (max_over_ranks(jms, world, device="cuda") / 1e3), "unit": "J-builds/s",
