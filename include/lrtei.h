@@ -150,6 +150,14 @@ lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d_idx4, int6
 lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d_s, double* d_w, double* d_c,
                            void* stream);
 
+/* ---- node sum of the factored form (Theorem 1, factored form; eq. approx33) ---------------
+ * d_K: n^3 x n^3 FP64, row-major, K((a1 n + a2) n + a3, (b1 n + b2) n + b3) =
+ * (omega / sqrt(pi)) sum_p w_p A_x^p(a1, b1) A_y^p(a2, b2) A_z^p(a3, b3), so that
+ * B_u = F_u K F_u^T.  For P <= 48 the node sum runs in pairs of FP32 numbers (compensated dot
+ * product), accurate to ~1e-13 of each row's largest entry; above, in FP64.  The tensor-core
+ * precisions slice this K.  Caller-owned output; LRTEI_ERR_ARG for NULL arguments. */
+lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream);
+
 /* ---- J-build (Section 5, eq. coulapprox in the density form J = mat(B vec(D))) ----------
  * d_D: R symmetric N_b x N_b densities (FP64, row-major, consecutive); d_J: same shape.
  * J_r(mu, nu) = sum_{ka, la} B(mu nu, ka la) D_r(ka, la), through the factored form, never
@@ -199,7 +207,8 @@ lrtei_status lrtei_selector_set_params(lrtei_selector* sel, const float* h_param
 /* ---- kernel timing (tracing) ----------------------------------------------------------
  * When enabled, the library records a pair of CUDA events on the launching stream around each
  * launch of its main kernels ("tc_gemm", "gemm_fp64", "gemm_fp32", "hadamard", "kron",
- * "expand_B", "moments", "build_F", "split", "jbuild").  lrtei_profile_get synchronises those
+ * "expand_B", "moments", "build_F", "build_K", "split", "jbuild", "batched" for a replayed
+ * J-build graph).  lrtei_profile_get synchronises those
  * events and returns the summed device time and the launch count of one kernel name.
  * Off by default; process-wide; not thread-safe against concurrent enable/reset. */
 lrtei_status lrtei_profile_enable(int on);

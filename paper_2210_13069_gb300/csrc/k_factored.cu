@@ -103,85 +103,111 @@ template void launch_build_F<double>(const PairTable&, int, const double*, int64
 template void launch_build_F<float>(const PairTable&, int, const double*, int64_t, int64_t, float*, int64_t,
                                     cudaStream_t);
 
-// K(a, b) with a = (a1 n + a2) n + a3, b likewise; one thread per entry.
-__global__ void k_build_K(int n, int P, const double* __restrict__ C, const double* __restrict__ w, double scale,
-                          double* __restrict__ K) {
-  const int n3 = n * n * n;
-  const int64_t total = (int64_t)n3 * n3;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(t / n3), b = (int)(t % n3);
-    const int a1 = a / (n * n), a2 = (a / n) % n, a3 = a % n;
-    const int b1 = b / (n * n), b2 = (b / n) % n, b3 = b % n;
-    const size_t nn = (size_t)n * n;
-    double acc = 0.0;
-    for (int p = 0; p < P; ++p) {
-      const double* cx = C + ((size_t)0 * P + p) * nn;
-      const double* cy = C + ((size_t)1 * P + p) * nn;
-      const double* cz = C + ((size_t)2 * P + p) * nn;
-      acc += w[p] * cx[a1 * n + b1] * cy[a2 * n + b2] * cz[a3 * n + b3];
-    }
-    K[t] = scale * acc;
-  }
+// The same K with the node sum in pairs of FP32 numbers (this part's FP32 rate is ~70 times its
+// FP64 rate; K only feeds 30-bit slices).  Each value is the unevaluated sum hi + lo of two floats
+// (Dekker 1971); a term r_p z_p is formed exactly in its leading part by an FMA (TwoProd) plus
+// the cross products, and summed by the compensated dot product Dot2 of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", 2005): the running sum by Knuth's TwoSum, the errors in a
+// second float.  The result, hi + lo in FP64, is accurate to ~2^-44 of the row maximum.
+//
+// Block (g tile, (a1, b1)): r_p(g) = scale w_p A_x^p(a1, b1) A_y^p(a2, b2) for kKG consecutive
+// g = (a2, b2) in shared memory (FP64, then split); thread t owns e = (a3, b3) in {t, t + blockDim}
+// (+ 2 blockDim ...) and the kKG outputs (g, e), reading z_p(e) = A_z^p(a3, b3) from a pair table
+// zp[p][e].  Sixteen independent sums per thread keep the FP32 pipes busy at modest occupancy;
+// consecutive threads write consecutive columns b3.
+constexpr int kKG = 8;  // g per pass (two passes of the block's 16-g tile)
+
+struct Pair32 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Pair32 to_pair(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
 }
 
-// The same K with one FMA per node and entry: block (a1, b1, part); thread (a3, b3) holds its P
-// values C_z^p(a3, b3) in registers; for each (a2, b2) the block shares r_p = scale w_p
-// C_x^p(a1, b1) C_y^p(a2, b2) through shared memory (kKGroup (a2, b2) at a time).  For fixed
-// (a2, b2) the block writes n-entry runs of consecutive columns.
-constexpr int kKGroup = 8;
-constexpr int kKThreads = 512;
-template <int PMAX>
-__global__ void __launch_bounds__(kKThreads) k_build_K_rows(int n, int P, int parts, const double* __restrict__ C,
-                                                            const double* __restrict__ w, double scale,
-                                                            double* __restrict__ K) {
-  __shared__ double r[kKGroup * PMAX];
+__global__ void k_K_zpairs(int nn, int P, const double* __restrict__ C, Pair32* __restrict__ zp) {
+  const int64_t total = (int64_t)nn * P;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    zp[i] = to_pair(C[(size_t)2 * P * nn + i]);  // zp[p][e] = A_z^p(e)
+}
+
+// One term of the compensated dot product (the _rn intrinsics are never contracted into FMAs,
+// which would break the exact steps).
+__device__ __forceinline__ void dot2_step(Pair32 x, Pair32 z, float& sum, float& err) {
+  const float ph = __fmul_rn(x.hi, z.hi);
+  float pe = fmaf(x.hi, z.hi, -ph);              // TwoProd: ph + pe = x.hi z.hi exactly
+  pe = fmaf(x.hi, z.lo, fmaf(x.lo, z.hi, pe));  // cross products (x.lo z.lo ~ 2^-48 dropped)
+  const float t = __fadd_rn(sum, ph);           // TwoSum: t + d = sum + ph exactly
+  const float bp = __fsub_rn(t, sum);
+  const float d = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
+  sum = t;
+  err = __fadd_rn(err, __fadd_rn(d, pe));
+}
+
+__global__ void __launch_bounds__(512, 1) k_build_K_tiled(int n, int P, const double* __restrict__ C,
+                                                       const double* __restrict__ w, const Pair32* __restrict__ zp,
+                                                       double scale, double* __restrict__ K) {
+  __shared__ Pair32 r[2 * kKG * kMaxP];
   const int nn = n * n;
   const int64_t n3 = (int64_t)nn * n;
-  const int ab = blockIdx.x / parts, part = blockIdx.x % parts;
-  const int a1 = ab / n, b1 = ab % n;
-  const int e = part * kKThreads + threadIdx.x;  // (a3, b3) = (e / n, e % n)
-  const bool live = e < nn;
-  const int a3 = e / n, b3 = e % n;
-  double cz[PMAX];
+  const int g0 = blockIdx.x * 2 * kKG;
+  const int ab = blockIdx.y, a1 = ab / n, b1 = ab % n;
+  for (int i = threadIdx.x; i < 2 * kKG * P; i += blockDim.x) {
+    const int g = g0 + i / P, p = i % P;
+    r[i] = to_pair(g < nn ? scale * w[p] * C[(size_t)p * nn + ab] * C[((size_t)P + p) * nn + g] : 0.0);
+  }
+  __syncthreads();
+  for (int half = 0; half < 2; ++half) {
+    const Pair32* rh = r + half * kKG * P;
+    const int gb = g0 + half * kKG;
+    if (gb >= nn) break;
+    for (int eb = 0; eb < nn; eb += 2 * blockDim.x) {
+      const int e0 = eb + threadIdx.x, e1 = e0 + blockDim.x;
+      const bool l0 = e0 < nn, l1 = e1 < nn;
+      if (!l0) break;
+      float sum[2][kKG], err[2][kKG];
 #pragma unroll
-  for (int p = 0; p < PMAX; ++p) cz[p] = (live && p < P) ? C[((size_t)2 * P + p) * nn + e] : 0.0;
-  for (int c0 = 0; c0 < nn; c0 += kKGroup) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kKGroup * P; i += blockDim.x) {
-      const int c = c0 + i / P, p = i % P;
-      r[(i / P) * PMAX + p] =
-          c < nn ? scale * w[p] * C[(size_t)p * nn + a1 * n + b1] * C[((size_t)P + p) * nn + c] : 0.0;
-    }
-    __syncthreads();
-    if (!live) continue;
-    for (int g = 0; g < kKGroup && c0 + g < nn; ++g) {
-      const int a2 = (c0 + g) / n, b2 = (c0 + g) % n;
-      double acc = 0.0;
+      for (int j = 0; j < kKG; ++j) sum[0][j] = err[0][j] = sum[1][j] = err[1][j] = 0.f;
+      for (int p = 0; p < P; ++p) {
+        const Pair32 z0 = zp[(size_t)p * nn + e0];
+        const Pair32 z1 = l1 ? zp[(size_t)p * nn + e1] : Pair32{0.f, 0.f};
 #pragma unroll
-      for (int p = 0; p < PMAX; ++p)
-        if (p < P) acc = fma(r[g * PMAX + p], cz[p], acc);
-      K[((int64_t)(a1 * n + a2) * n + a3) * n3 + ((int64_t)(b1 * n + b2) * n + b3)] = acc;
+        for (int j = 0; j < kKG; ++j) {
+          const Pair32 x = rh[j * P + p];
+          dot2_step(x, z0, sum[0][j], err[0][j]);
+          dot2_step(x, z1, sum[1][j], err[1][j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kKG; ++j) {
+        const int g = gb + j;
+        if (g >= nn) break;
+        const int a2 = g / n, b2 = g % n;
+        const int64_t row0 = (int64_t)(a1 * n + a2) * n, col0 = (int64_t)(b1 * n + b2) * n;
+        K[(row0 + e0 / n) * n3 + col0 + e0 % n] = (double)sum[0][j] + (double)err[0][j];
+        if (l1) K[(row0 + e1 / n) * n3 + col0 + e1 % n] = (double)sum[1][j] + (double)err[1][j];
+      }
     }
   }
 }
 
-void launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K, cudaStream_t st) {
-  const int64_t n3 = (int64_t)n * n * n;
+cudaError_t launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K,
+                           cudaStream_t st) {
   const int nn = n * n;
+  Pair32* zp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&zp, sizeof(Pair32) * (size_t)nn * P, st);
+  if (e != cudaSuccess) return e;
   count_launch();
-  if (P <= 48) {
-    const int parts = (nn + kKThreads - 1) / kKThreads;
-    const int threads = std::min(kKThreads, (nn + 31) / 32 * 32);
-    const unsigned blocks = (unsigned)(nn * parts);
-    if (P <= 32)
-      k_build_K_rows<32><<<blocks, threads, 0, st>>>(n, P, parts, d_C, d_w, scale, d_K);
-    else
-      k_build_K_rows<48><<<blocks, threads, 0, st>>>(n, P, parts, d_C, d_w, scale, d_K);
-    return;
-  }
-  int64_t blocks = (n3 * n3 + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_build_K<<<(unsigned)blocks, 256, 0, st>>>(n, P, d_C, d_w, scale, d_K);
+  k_K_zpairs<<<(unsigned)std::min<int64_t>(((int64_t)nn * P + 255) / 256, 152 * 8), 256, 0, st>>>(nn, P, d_C, zp);
+  // two e per thread; at most 512 threads
+  const int threads = std::min(512, ((nn + 1) / 2 + 31) / 32 * 32);
+  count_launch();
+  k_build_K_tiled<<<dim3((unsigned)((nn + 2 * kKG - 1) / (2 * kKG)), (unsigned)nn), threads, 0, st>>>(n, P, d_C, d_w, zp,
+                                                                                                     scale, d_K);
+  e = cudaGetLastError();
+  cudaFreeAsync(zp, st);
+  return e;
 }
 
 // Mode product on a tensor viewed as (I, n, Kd): out[i][a][k] = sum_m C[a][m] in[i][m][k].

@@ -557,7 +557,10 @@ lrtei_status ensure_Ksp(lrtei_plan* pl, cudaStream_t st, bool need_s1h) {
   Scratch sc(st);
   double* K;
   LRTEI_TRY(sc.get(&K, (size_t)n3 * n3));
-  launch_build_K(pl->n, pl->P, pl->d_C, pl->d_w, pl->omega / sqrt(kPi), K, st);
+  {
+    ProfScope ps("build_K", st);
+    LRTEI_CUDA(launch_build_K(pl->n, pl->P, pl->d_C, pl->d_w, pl->omega / sqrt(kPi), K, st));
+  }
   LRTEI_TRY(alloc_split(pl, pl->Ksp, n3, n3, need_s1h));
   {
     ProfScope ps("split", st);
@@ -1037,6 +1040,16 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
   if (d_w) LRTEI_CUDA(cudaMemcpyAsync(d_w, plan->d_w, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
   if (d_c) LRTEI_CUDA(cudaMemcpyAsync(d_c, plan->t.row_c, sizeof(double) * nrows, cudaMemcpyDeviceToDevice, st));
   return LRTEI_OK;
+}
+
+lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream) {
+  if (!plan || !d_K) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  {
+    ProfScope ps("build_K", (cudaStream_t)stream);
+    LRTEI_CUDA(launch_build_K(plan->n, plan->P, plan->d_C, plan->d_w, plan->omega / sqrt(kPi), d_K,
+                              (cudaStream_t)stream));
+  }
+  return finish_launch("dense K");
 }
 
 static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st) {

@@ -115,7 +115,8 @@ template <typename T>
 void launch_build_F(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, T* d_F, int64_t ldF,
                     cudaStream_t st);
 // Dense K = sum_p w_p C_x^p (x) C_y^p (x) C_z^p  (n^3 x n^3), FP64.
-void launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K, cudaStream_t st);
+cudaError_t launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K,
+                           cudaStream_t st);
 // Y = sum_p w_p (C_x^p (x) C_y^p (x) C_z^p) X, X/Y: n^3 x ncol (column index fastest).
 void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const double* d_X, double* d_Y,
                        int64_t ncol, double* d_t1, double* d_t2, cudaStream_t st);

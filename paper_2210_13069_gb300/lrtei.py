@@ -73,6 +73,7 @@ def load():
         "lrtei_entries": (S, [VP, VP, ctypes.c_int64, VP, VP]),
         "lrtei_entries_noalloc": (S, [VP, VP, ctypes.c_int64, VP, VP]),
         "lrtei_factors": (S, [VP, VP, VP, VP, VP, VP, VP]),
+        "lrtei_dense_K": (S, [VP, VP, VP]),
         "lrtei_jbuild": (S, [VP, VP, ctypes.c_int, VP, VP]),
         "lrtei_jbuild_batched": (S, [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(VP), IP, ctypes.POINTER(VP),
                                      VP]),
@@ -197,6 +198,10 @@ def lrtei_entries_noalloc(plan: int, d_idx4, count: int, d_out, stream=None):
 
 def lrtei_factors(plan: int, d_S=None, d_C=None, d_s=None, d_w=None, d_c=None, stream=None):
     _check(load().lrtei_factors(plan, _ptr(d_S), _ptr(d_C), _ptr(d_s), _ptr(d_w), _ptr(d_c), _stream(stream)))
+
+
+def lrtei_dense_K(plan: int, d_K, stream=None):
+    _check(load().lrtei_dense_K(plan, _ptr(d_K), _stream(stream)))
 
 
 def lrtei_jbuild(plan: int, d_D, R: int, d_J, stream=None):
@@ -358,6 +363,13 @@ class Plan:
         c = torch.empty(nrows, dtype=torch.float64, device="cuda")
         lrtei_factors(self.plan, S, C, s, w, c, stream)
         return S, C, s, w, c
+
+    def dense_K(self, stream=None):
+        torch = self._torch
+        n3 = self.info["n"] ** 3
+        K = torch.empty((n3, n3), dtype=torch.float64, device="cuda")
+        lrtei_dense_K(self.plan, K, stream)
+        return K
 
     def jbuild(self, D, out=None, stream=None):
         torch = self._torch

@@ -426,3 +426,45 @@ def test_streamed_jbuild_matches_one_pass(lib, precision, monkeypatch):
         if precision == "fp64":
             assert rel_fro(J, J1) <= 1e-13
     pl.close()
+
+
+def _K_rows(omega, n, w, C, rows):
+    """Rows (a1 n + a2) n + a3 of (omega / sqrt(pi)) sum_p w_p A_x^p (x) A_y^p (x) A_z^p from the
+    weights w[p] and the Chebyshev coefficient matrices C[d][p] (n x n)."""
+    out = np.zeros((len(rows), n ** 3))
+    for i, row in enumerate(rows):
+        a1, a2, a3 = row // (n * n), (row // n) % n, row % n
+        for p in range(len(w)):
+            out[i] += w[p] * np.kron(C[0][p][a1], np.kron(C[1][p][a2], C[2][p][a3]))
+    return out * omega / np.sqrt(np.pi)
+
+
+@pytest.mark.parametrize("n,P", [(12, 12), (7, 40), (6, 60), (24, 32)])
+def test_dense_K_matches_oracle_factors(lib, n, P):
+    """The dense node sum K of the factored form (pairs of FP32 numbers for P <= 48, FP64 above).
+    Its arithmetic: against K formed in FP64 from the plan's own weights and coefficients, every
+    entry within 2e-13 of its row's largest entry.  Against the oracle's weights and coefficients
+    within 1e-11: the weights agree to 1e-13 relative and an entry sums terms up to ~18 times the
+    row maximum.  Full K for small n, sampled rows at n = 24."""
+    m = mol_spd_small(n=n, P=P)
+    o = oracle.Oracle.from_molecule(m)
+    pl = lib.Plan(m, "split_f16")
+    K = pl.dense_K()
+    _, Cg, _, wg, _ = [t.cpu().numpy() for t in pl.factors()]
+    pl.status()
+    n3 = n ** 3
+    rows = list(range(n3)) if n3 <= 2000 else [0, 1, n3 // 3, n3 // 2 + 7, n3 - 1]
+    got = K[rows].cpu().numpy() if n3 > 2000 else K.cpu().numpy()
+    _, wo = o.nodes()
+    Co = [[o.cheb(d, p) for p in range(P)] for d in range(3)]
+    ref_plan = _K_rows(m.omega, n, wg, Cg, rows)
+    ref_oracle = _K_rows(o.omega, n, wo, Co, rows)
+    scale = np.abs(ref_oracle).max(axis=1, keepdims=True)
+    err_plan = float((np.abs(got - ref_plan) / scale).max())
+    err_oracle = float((np.abs(got - ref_oracle) / scale).max())
+    print(f"dense K n={n} P={P}: max |error| / row max = {err_plan:.2e} (plan factors), {err_oracle:.2e} (oracle)")
+    assert err_plan <= 2e-13
+    assert err_oracle <= 1e-11
+    if n3 <= 2000:
+        assert np.allclose(got, got.T, rtol=0, atol=1e-12 * np.abs(ref_oracle).max())
+    pl.close()
