@@ -153,9 +153,9 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
 /* ---- node sum of the factored form (Theorem 1, factored form; eq. approx33) ---------------
  * d_K: n^3 x n^3 FP64, row-major, K((a1 n + a2) n + a3, (b1 n + b2) n + b3) =
  * (omega / sqrt(pi)) sum_p w_p A_x^p(a1, b1) A_y^p(a2, b2) A_z^p(a3, b3), so that
- * B_u = F_u K F_u^T.  For P <= 48 the node sum runs in pairs of FP32 numbers (compensated dot
- * product), accurate to ~1e-13 of each row's largest entry; above, in FP64.  The tensor-core
- * precisions slice this K.  Caller-owned output; LRTEI_ERR_ARG for NULL arguments. */
+ * B_u = F_u K F_u^T.  The node sum runs in pairs of FP32 numbers (TwoProd and a compensated dot
+ * product), accurate to ~1e-13 of each row's largest entry; the tensor-core precisions slice this
+ * K.  Caller-owned output; LRTEI_ERR_ARG for NULL arguments. */
 lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream);
 
 /* ---- J-build (Section 5, eq. coulapprox in the density form J = mat(B vec(D))) ----------

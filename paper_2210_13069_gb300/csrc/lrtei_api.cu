@@ -974,7 +974,12 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
     cudaError_t e = cudaPointerGetAttributes(&pa, d_B);
     if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(B)");
     if (pa.type == cudaMemoryTypeHost) {
-      if (!pa.devicePointer) { set_error("pinned host B is not mapped into the device address space"); return LRTEI_ERR_ARG; }
+      // copy engines move B on the tensor-core path; the FP64 / FP32 expansion stores through the
+      // buffer's device alias
+      if (!pa.devicePointer && !is_split(plan)) {
+        set_error("pinned host B is not mapped into the device address space");
+        return LRTEI_ERR_ARG;
+      }
       hB = d_B;
       d_B = static_cast<double*>(pa.devicePointer);
     } else if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) {

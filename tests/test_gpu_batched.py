@@ -90,3 +90,24 @@ def test_batched_graph_after_operands_rebuilt(lib):
     for p in plans:
         p.status()
         p.close()
+
+
+def test_graph_cache_keeps_at_most_32_and_recaptures(lib):
+    """Thirty-five distinct J-build calls (one plan, one density batch, 35 output buffers) each
+    leave a captured graph; the cache keeps the 32 most recent, so the first calls' graphs are
+    dropped and recaptured when they come again, with the same results."""
+    import torch
+    m = small_batch()[1]
+    pl = lib.Plan(m, "split_f16")
+    D = torch.as_tensor(synth.random_densities(810, m.nbf, 3), device="cuda")
+    ref = pl.jbuild(D)
+    outs = [torch.empty_like(D) for _ in range(35)]
+    for rep in range(3):  # run and capture, then replay (with evictions in between)
+        for J in outs:
+            J.fill_(float("nan"))
+            pl.jbuild(D, out=J)
+        torch.cuda.synchronize()
+        for J in outs:
+            assert torch.equal(J, ref), rep
+    pl.status()
+    pl.close()

@@ -441,8 +441,9 @@ def _K_rows(omega, n, w, C, rows):
 
 @pytest.mark.parametrize("n,P", [(12, 12), (7, 40), (6, 60), (24, 32)])
 def test_dense_K_matches_oracle_factors(lib, n, P):
-    """The dense node sum K of the factored form (pairs of FP32 numbers for P <= 48, FP64 above).
-    Its arithmetic: against K formed in FP64 from the plan's own weights and coefficients, every
+    """The dense node sum K of the factored form (pairs of FP32 numbers, any P; P = 60 spans
+    more nodes than one 32-wide pass).  Its arithmetic: against K formed in FP64 from the plan's
+    own weights and coefficients, every
     entry within 2e-13 of its row's largest entry.  Against the oracle's weights and coefficients
     within 1e-11: the weights agree to 1e-13 relative and an entry sums terms up to ~18 times the
     row maximum.  Full K for small n, sampled rows at n = 24."""
