@@ -236,6 +236,48 @@ def cpu_oracle_rate(mol, budget_s: float, seed: int = 99):
     return total_entries / total_t, threads, f"{total_entries} random entries (mu,nu,ka,la) of B, Algorithm 1 per entry incl. their pair moments, {total_t:.1f} s"
 
 
+# ------------------------------------------------------------------ screening leg
+
+def run_screening(args, mol, B, tau=1e-10):
+    """Plan creation plus the first B (moments, F_u and K built on the way), best of three, without
+    and with primitive-pair screening at tau; the rows kept; the relative change of B."""
+    import torch
+
+    from paper_2210_13069_gb300 import lrtei
+    out = {"tau_screening": tau}
+    B2 = torch.empty_like(B)
+    for key, t, dst in (("tau0", 0.0, B), ("tau", tau, B2)):
+        best = None
+        for _ in range(3):
+            lrtei.lrtei_profile_reset()
+            lrtei.lrtei_profile_enable(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p = lrtei.Plan(mol, args.precision, tau_screening=t)
+            p.assemble_B(args.form, out=dst)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            prof = {k: lrtei.lrtei_profile_get(k)[0] for k in ("moments", "build_F")}
+            lrtei.lrtei_profile_enable(False)
+            rows = p.info["nrows"]
+            p.status()
+            p.close()
+            if best is None or dt < best["plan_plus_first_B_s"]:
+                best = {"plan_plus_first_B_s": dt, "rows": rows, "moments_ms": prof["moments"],
+                        "build_F_ms": prof["build_F"]}
+        out[key] = best
+    out["rows_kept_fraction"] = out["tau"]["rows"] / out["tau0"]["rows"]
+    num = den = 0.0
+    for i in range(0, B.shape[0], 4096):  # in row blocks: no full-size temporary
+        num += float(torch.linalg.norm(B2[i:i + 4096] - B[i:i + 4096])) ** 2
+        den += float(torch.linalg.norm(B[i:i + 4096])) ** 2
+    out["rel_change_of_B"] = math.sqrt(num / den)
+    lrtei.lrtei_profile_reset()
+    del B2
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, world, rank, local):
@@ -488,6 +530,11 @@ def run_ours(args, world, rank, local):
         split8 = {"entries_per_s": whole_job_rate(entries_per_step, world, ms8, device="cuda"), "ms_per_step": ms8}
         p8.close()
 
+    # ---- primitive-pair screening (Section 6) at the paper's tau = 1e-10: rows kept, plan set-up
+    screening = None
+    if args.natoms == 12 and not args.no_fp64:
+        screening = run_screening(args, mol, B)
+
     # ---- batched J-builds: 64 molecules of uneven size, 16 densities each
     batched = None
     if not args.no_batched and args.precision in ("split_f16", "split_f16_8", "bf16"):
@@ -567,7 +614,7 @@ def run_ours(args, world, rank, local):
                        "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
-            "jbuilds": jb, "fp64_same_gpu": fp64, "split_f16_8": split8, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "jbuilds": jb, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)

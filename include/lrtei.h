@@ -86,6 +86,7 @@ typedef struct {
   int precision;    /* lrtei_precision */
   int last_form;    /* lrtei_form used by the last lrtei_assemble_B call */
   size_t workspace_bytes; /* device bytes the plan currently holds */
+  double tau_screening;   /* primitive-pair screening threshold of the plan (0: none) */
 } lrtei_plan_info;
 
 /* ---- basis (Section 1, eq. "basis"/"primi") ------------------------------------------
@@ -104,6 +105,15 @@ int lrtei_basis_nbf(const lrtei_basis* basis);
  * omega > 0; 1 <= n <= 64; 1 <= P <= 128; box_lo/box_hi: 3 doubles each or both NULL. */
 lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
                                const double* box_hi, lrtei_precision precision, void* stream, lrtei_plan** out);
+/* The same with primitive-pair screening (Section 6, "Compression by using Screening"): the
+ * primitive pair (j1, j2) of a basis pair (mu, nu) is discarded when
+ * exp(-a_j1 b_j2 / (a_j1 + b_j2) |A - B|^2) <= tau_screening (exponents a, b, centres A, B),
+ * decided on the host in FP64; its row leaves the pair table, so the moments, F_u and every
+ * sum over j skip it.  tau_screening in [0, 1]; 0 keeps every pair (lrtei_plan_create).
+ * lrtei_factors then returns the kept rows only, in the same order. */
+lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
+                                  const double* box_hi, lrtei_precision precision, double tau_screening,
+                                  void* stream, lrtei_plan** out);
 void lrtei_plan_destroy(lrtei_plan* plan);
 lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info);
 /* Synchronises the plan's stream and returns the latched device-side status (then clears it). */

@@ -51,6 +51,7 @@ def load_library(path: str):
     lib.orc_create.restype = ctypes.c_void_p
     lib.orc_create.argtypes = [ctypes.c_int, D, I, I, D, D, ctypes.c_double, ctypes.c_int, ctypes.c_int, D, D]
     lib.orc_destroy.argtypes = [ctypes.c_void_p]
+    lib.orc_set_screening.argtypes = [ctypes.c_void_p, ctypes.c_double]
     lib.orc_nbf.argtypes = [ctypes.c_void_p]
     lib.orc_nbf.restype = ctypes.c_int
     lib.orc_box.argtypes = [ctypes.c_void_p, D, D]
@@ -93,7 +94,8 @@ class Oracle:
     """One molecule + (omega, n, P, box) on the CPU, FP64."""
 
     def __init__(self, centers, ls, nprim, exps, coefs, omega: float, n: int, P: int,
-                 box_lo: Optional[Sequence[float]] = None, box_hi: Optional[Sequence[float]] = None, lib=None):
+                 box_lo: Optional[Sequence[float]] = None, box_hi: Optional[Sequence[float]] = None, lib=None,
+                 tau_screening: float = 0.0):
         lib = lib or _load()
         self._lib = lib
         self._keep = [np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3),
@@ -110,6 +112,9 @@ class Oracle:
             raise ValueError("oracle rejected the input")
         self.omega, self.n, self.P = float(omega), int(n), int(P)
         self.nbf = lib.orc_nbf(self._h)
+        self.tau_screening = float(tau_screening)
+        if tau_screening:
+            lib.orc_set_screening(self._h, float(tau_screening))
 
     @classmethod
     def from_molecule(cls, mol, **kw):
@@ -117,7 +122,7 @@ class Oracle:
         lo = kw.pop("box_lo", mol.box_lo)
         hi = kw.pop("box_hi", mol.box_hi)
         return cls(centers, ls, nprim, exps, coefs, kw.pop("omega", mol.omega), kw.pop("n", mol.n),
-                   kw.pop("P", mol.P), box_lo=lo, box_hi=hi)
+                   kw.pop("P", mol.P), box_lo=lo, box_hi=hi, tau_screening=kw.pop("tau_screening", 0.0))
 
     def __del__(self):
         h = getattr(self, "_h", None)

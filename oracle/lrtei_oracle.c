@@ -54,6 +54,7 @@ struct orc_ctx {
   double* A;   /* 3 * P * n * n */
   double qz[ORC_QPTS], qw[ORC_QPTS];
   double** mom;         /* nbf*nbf*3 slots, each (I_mu I_nu) x n, lazily filled */
+  double tau_screening; /* primitive-pair screening threshold (0: keep every pair) */
 };
 
 /* ---------------------------------------------------------------- small helpers ---- */
@@ -222,6 +223,8 @@ void orc_destroy(orc_ctx* c) {
   free(c);
 }
 
+void orc_set_screening(orc_ctx* c, double tau) { c->tau_screening = tau; }
+
 int orc_nbf(const orc_ctx* c) { return c->nbf; }
 
 void orc_box(const orc_ctx* c, double* lo3, double* hi3) {
@@ -348,6 +351,20 @@ static void ensure_moments(orc_ctx* c, const int64_t* pairs, int64_t npairs, int
 
 /* --------------------------------------------------------------- Algorithm 1 ---- */
 
+/* c_j = c_{j1} c_{j2} of the primitive pair (j1, j2) of (mu, nu) (eq. approx4), or 0 when the pair
+   is discarded by screening (Section 6, "Compression by using Screening"):
+   exp(-a b / (a + b) |A - B|^2) <= tau_screening with a, b the two exponents and A, B the two
+   centres.  A discarded pair contributes nothing to any sum over j. */
+static double pair_coef(const orc_ctx* c, const orc_bf* f1, const orc_bf* f2, int j1, int j2) {
+  if (c->tau_screening > 0.0) {
+    const double a = f1->exps[j1], b = f2->exps[j2];
+    double d2 = 0.0;
+    for (int l = 0; l < 3; ++l) d2 += (f1->center[l] - f2->center[l]) * (f1->center[l] - f2->center[l]);
+    if (exp(-(a * b / (a + b)) * d2) <= c->tau_screening) return 0.0;
+  }
+  return f1->coefs[j1] * f2->coefs[j2];
+}
+
 static double entry_cached(const orc_ctx* c, int mu, int nu, int ka, int la) {
   const int n = c->n, P = c->P;
   const orc_bf *f1 = &c->bf[mu], *f2 = &c->bf[nu], *g1 = &c->bf[ka], *g2 = &c->bf[la];
@@ -359,9 +376,9 @@ static double entry_cached(const orc_ctx* c, int mu, int nu, int ka, int la) {
   double* F = G + (size_t)I1 * I2;
   /* c_j = c_{j1} c_{j2} (eq. approx4) */
   for (int j1 = 0; j1 < f1->nprim; ++j1)
-    for (int j2 = 0; j2 < f2->nprim; ++j2) cj[j1 * f2->nprim + j2] = f1->coefs[j1] * f2->coefs[j2];
+    for (int j2 = 0; j2 < f2->nprim; ++j2) cj[j1 * f2->nprim + j2] = pair_coef(c, f1, f2, j1, j2);
   for (int j1 = 0; j1 < g1->nprim; ++j1)
-    for (int j2 = 0; j2 < g2->nprim; ++j2) cjp[j1 * g2->nprim + j2] = g1->coefs[j1] * g2->coefs[j2];
+    for (int j2 = 0; j2 < g2->nprim; ++j2) cjp[j1 * g2->nprim + j2] = pair_coef(c, g1, g2, j1, j2);
 
   double s = 0.0, comp = 0.0; /* Neumaier-compensated sum over the nodes */
   for (int p = 0; p < P; ++p) {
@@ -466,7 +483,7 @@ static void factor_row(const orc_ctx* c, int mu, int nu, double* row) {
   for (int j1 = 0; j1 < f1->nprim; ++j1)
     for (int j2 = 0; j2 < f2->nprim; ++j2) {
       int j = j1 * f2->nprim + j2;
-      double cj = f1->coefs[j1] * f2->coefs[j2];
+      double cj = pair_coef(c, f1, f2, j1, j2);
       for (int m1 = 0; m1 < n; ++m1)
         for (int m2 = 0; m2 < n; ++m2)
           for (int m3 = 0; m3 < n; ++m3)

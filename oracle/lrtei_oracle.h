@@ -32,6 +32,10 @@ orc_ctx* orc_create(int nshells, const double* centers, const int* l, const int*
                     const double* exps, const double* coefs, double omega, int n, int P,
                     const double* box_lo, const double* box_hi);
 void orc_destroy(orc_ctx* c);
+/* Primitive-pair screening (Section 6, "Compression by using Screening"): from now on the
+   primitive pair (j1, j2) of (mu, nu) with exp(-a b / (a + b) |A - B|^2) <= tau is discarded (its
+   c_j is taken as 0 in every sum over j).  tau = 0 (the default) keeps every pair. */
+void orc_set_screening(orc_ctx* c, double tau);
 
 int orc_nbf(const orc_ctx* c);
 void orc_box(const orc_ctx* c, double* lo3, double* hi3);

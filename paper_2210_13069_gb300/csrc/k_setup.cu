@@ -161,6 +161,7 @@ void launch_normalise(int nbf, const int* d_bf_shell, const int* d_bf_pow, const
 // One block per unique pair (mu <= nu); threads over its I_mu I_nu primitive pairs.
 // Gaussian product rule (Proposition 1): exp(-a(x-A)^2) exp(-b(x-B)^2) = K_AB exp(-p (x-P)^2).
 __global__ void k_pair_rows(int64_t npair, const int* pair_mu, const int* pair_nu, const int64_t* pair_row,
+                            const int* pair_I, const uint8_t* row_prim,
                             const int* bf_shell, const int* bf_pow, const int* shell_nprim, const int* shell_poff,
                             const double* shell_center, const double* exps, const int* bf_coff,
                             const double* ncoef, int64_t nrows, int* row_pair, double* row_c, double* row_p,
@@ -170,11 +171,10 @@ __global__ void k_pair_rows(int64_t npair, const int* pair_mu, const int* pair_n
   if (r >= npair) return;
   const int mu = pair_mu[r], nu = pair_nu[r];
   const int sm = bf_shell[mu], sn = bf_shell[nu];
-  const int Km = shell_nprim[sm], Kn = shell_nprim[sn];
   const int64_t base = pair_row[r];
-  for (int j = threadIdx.x; j < Km * Kn; j += blockDim.x) {
-    const int j1 = j / Kn, j2 = j % Kn;
+  for (int j = threadIdx.x; j < pair_I[r]; j += blockDim.x) {  // the pair's kept primitive pairs
     const int64_t row = base + j;
+    const int j1 = row_prim[row] >> 4, j2 = row_prim[row] & 15;
     const double a = exps[shell_poff[sm] + j1], b = exps[shell_poff[sn] + j2];
     const double p = a + b;
     row_pair[row] = (int)r;
@@ -196,7 +196,8 @@ void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf
                       const int* d_shell_poff, const double* d_shell_center, const double* d_exps,
                       const int* d_bf_coff, const double* d_ncoef, cudaStream_t st) {
   count_launch();
-  k_pair_rows<<<(unsigned)t.npair, 64, 0, st>>>(t.npair, t.pair_mu, t.pair_nu, t.pair_row, d_bf_shell, d_bf_pow,
+  k_pair_rows<<<(unsigned)t.npair, 64, 0, st>>>(t.npair, t.pair_mu, t.pair_nu, t.pair_row, t.pair_I, t.row_prim,
+                                                d_bf_shell, d_bf_pow,
                                                 d_shell_nprim, d_shell_poff, d_shell_center, d_exps, d_bf_coff,
                                                 d_ncoef, t.nrows, t.row_pair, t.row_c, t.row_p, t.row_P, t.row_K,
                                                 t.row_A, t.row_B, t.row_pa, t.row_pb);
@@ -288,10 +289,10 @@ __global__ void k_moment_keys(const PairTable t, const int* __restrict__ bf_shel
     const int mu = t.pair_mu[r], nu = t.pair_nu[r];
     const int s1 = bf_shell[mu], s2 = bf_shell[nu];
     const int Kn = shell_nprim[s2];
-    const int j = (int)(row - t.pair_row[r]);
+    const int j1 = t.row_prim[row] >> 4, j2 = t.row_prim[row] & 15;
     const int lb = shell_l[s2] + 1, cmb = (shell_l[s1] + 1) * lb;
     const int64_t tri = (int64_t)s1 * nshells - (int64_t)s1 * (s1 - 1) / 2 + (s2 - s1);
-    const int64_t base = sp_off[tri] + (int64_t)((j / Kn) * Kn + j % Kn) * 3 * cmb;
+    const int64_t base = sp_off[tri] + (int64_t)(j1 * Kn + j2) * 3 * cmb;
     for (int d = 0; d < 3; ++d) {
       const int64_t u = base + d * cmb + bf_pow[3 * mu + d] * lb + bf_pow[3 * nu + d];
       key[d * t.nrows + row] = (int)u;

@@ -56,6 +56,7 @@ struct lrtei_plan {
   int n = 0, P = 0;
   double lo[3], hi[3];
   lrtei_precision prec = LRTEI_FP64;
+  double tau = 0.0;  // primitive-pair screening threshold
   int last_form = 0;
   PairTable t;
   // device data
@@ -178,7 +179,17 @@ int lrtei_basis_nbf(const lrtei_basis* basis) { return basis ? basis->nbf : 0; }
 
 lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
                                const double* box_hi, lrtei_precision precision, void* stream, lrtei_plan** out) {
+  return lrtei_plan_create_ex(basis, omega, n, P, box_lo, box_hi, precision, 0.0, stream, out);
+}
+
+lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
+                                  const double* box_hi, lrtei_precision precision, double tau_screening,
+                                  void* stream, lrtei_plan** out) {
   if (!out) { set_error("out is NULL"); return LRTEI_ERR_ARG; }
+  if (!(tau_screening >= 0.0 && tau_screening <= 1.0)) {
+    set_error("tau_screening must be in [0, 1] (got %g)", tau_screening);
+    return LRTEI_ERR_ARG;
+  }
   *out = nullptr;
   if (!basis) { set_error("basis is NULL"); return LRTEI_ERR_ARG; }
   if (!(omega > 0.0) || !isfinite(omega)) { set_error("omega must be > 0 (got %g)", omega); return LRTEI_ERR_ARG; }
@@ -200,6 +211,7 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   pl->n = n;
   pl->P = P;
   pl->prec = precision;
+  pl->tau = tau_screening;
   const lrtei_basis& b = pl->basis;
   // box (eq. compact)
   if (box_lo) {
@@ -232,14 +244,28 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   const int nbf = b.nbf;
   PairTable& t = pl->t;
   t.npair = npair_of(nbf);
+  // Rows are the primitive pairs (j1, j2) of each unique pair, j1 of mu's shell major; with
+  // screening (Section 6) a primitive pair with exp(-a b / (a + b) |A - B|^2) <= tau is left out.
   std::vector<int> pmu(t.npair), pnu(t.npair), pI(t.npair);
   std::vector<int64_t> prow(t.npair + 1);
+  std::vector<uint8_t> rprim;
   int64_t r = 0, rows = 0;
   for (int mu = 0; mu < nbf; ++mu)
     for (int nu = mu; nu < nbf; ++nu) {
+      const int s1 = b.bf_shell[mu], s2 = b.bf_shell[nu];
+      double d2 = 0.0;
+      for (int l = 0; l < 3; ++l) d2 += (b.centers[3 * s1 + l] - b.centers[3 * s2 + l]) * (b.centers[3 * s1 + l] - b.centers[3 * s2 + l]);
+      int kept = 0;
+      for (int j1 = 0; j1 < b.nprim[s1]; ++j1)
+        for (int j2 = 0; j2 < b.nprim[s2]; ++j2) {
+          const double a = b.exps[b.poff[s1] + j1], e = b.exps[b.poff[s2] + j2];
+          if (tau_screening > 0.0 && exp(-(a * e / (a + e)) * d2) <= tau_screening) continue;
+          rprim.push_back((uint8_t)((j1 << 4) | j2));
+          ++kept;
+        }
       pmu[r] = mu;
       pnu[r] = nu;
-      pI[r] = b.nprim[b.bf_shell[mu]] * b.nprim[b.bf_shell[nu]];
+      pI[r] = kept;
       t.maxI = std::max(t.maxI, pI[r]);
       prow[r] = rows;
       rows += pI[r];
@@ -284,6 +310,7 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   PA(t.row_B, 3 * t.nrows);
   PA(t.row_pa, 3 * t.nrows);
   PA(t.row_pb, 3 * t.nrows);
+  PA(t.row_prim, t.nrows);
 #undef PA
   double half3[3];
   for (int d = 0; d < 3; ++d) half3[d] = 0.5 * (pl->hi[d] - pl->lo[d]);
@@ -307,6 +334,7 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   UP(t.pair_nu, pnu.data(), t.npair);
   UP(t.pair_row, prow.data(), t.npair + 1);
   UP(t.pair_I, pI.data(), t.npair);
+  if (t.nrows > 0) UP(t.row_prim, rprim.data(), t.nrows);
 #undef UP
   // The uploads above are from pageable memory: they complete (staged) before returning.
   ce = cudaMemsetAsync(pl->d_status, 0, sizeof(int), st);
@@ -389,6 +417,7 @@ lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info) 
   info->precision = plan->prec;
   info->last_form = plan->last_form;
   info->workspace_bytes = plan->bytes;
+  info->tau_screening = plan->tau;
   return LRTEI_OK;
 }
 

@@ -52,7 +52,8 @@ struct PairTable {
   int* pair_mu = nullptr;      // [npair]
   int* pair_nu = nullptr;      // [npair]
   int64_t* pair_row = nullptr; // [npair + 1] first row of each pair
-  int* pair_I = nullptr;       // [npair] rows of each pair (I_mu I_nu)
+  int* pair_I = nullptr;       // [npair] rows of each pair (I_mu I_nu, fewer when screened)
+  uint8_t* row_prim = nullptr; // [nrows] (j1 << 4) | j2: the primitives of mu and nu of each row
   // per row
   int* row_pair = nullptr;     // [nrows]
   double* row_c = nullptr;     // [nrows] c_j = c_{j1} c_{j2} (normalised)

@@ -37,7 +37,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("nbf", ctypes.c_int), ("npair", ctypes.c_int64), ("nrows", ctypes.c_int64), ("n", ctypes.c_int),
                 ("P", ctypes.c_int), ("omega", ctypes.c_double), ("box_lo", ctypes.c_double * 3),
                 ("box_hi", ctypes.c_double * 3), ("precision", ctypes.c_int), ("last_form", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("tau_screening", ctypes.c_double)]
 
 
 _lib = None
@@ -65,6 +65,8 @@ def load():
         "lrtei_basis_nbf": (ctypes.c_int, [VP]),
         "lrtei_plan_create": (S, [VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, DP, DP, ctypes.c_int, VP,
                                   ctypes.POINTER(VP)]),
+        "lrtei_plan_create_ex": (S, [VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, DP, DP, ctypes.c_int,
+                                     ctypes.c_double, VP, ctypes.POINTER(VP)]),
         "lrtei_plan_destroy": (None, [VP]),
         "lrtei_plan_info_get": (S, [VP, ctypes.POINTER(PlanInfo)]),
         "lrtei_plan_status": (S, [VP]),
@@ -161,6 +163,21 @@ def lrtei_plan_create(basis: int, omega: float, n: int, P: int, box_lo=None, box
     return out.value
 
 
+def lrtei_plan_create_ex(basis: int, omega: float, n: int, P: int, box_lo=None, box_hi=None,
+                         precision: int = LRTEI_FP64, tau_screening: float = 0.0, stream=None) -> int:
+    lib = load()
+    lo = hi = None
+    if box_lo is not None:
+        lo = _np(box_lo, np.float64)
+        hi = _np(box_hi, np.float64)
+    out = VP()
+    _check(lib.lrtei_plan_create_ex(basis, float(omega), int(n), int(P),
+                                    lo.ctypes.data_as(DP) if lo is not None else None,
+                                    hi.ctypes.data_as(DP) if hi is not None else None, int(precision),
+                                    float(tau_screening), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
 def lrtei_plan_destroy(plan: int):
     load().lrtei_plan_destroy(plan)
 
@@ -170,7 +187,8 @@ def lrtei_plan_info_get(plan: int) -> dict:
     _check(load().lrtei_plan_info_get(plan, ctypes.byref(info)))
     return {"nbf": info.nbf, "npair": info.npair, "nrows": info.nrows, "n": info.n, "P": info.P,
             "omega": info.omega, "box_lo": list(info.box_lo), "box_hi": list(info.box_hi),
-            "precision": info.precision, "last_form": info.last_form, "workspace_bytes": info.workspace_bytes}
+            "precision": info.precision, "last_form": info.last_form, "workspace_bytes": info.workspace_bytes,
+            "tau_screening": info.tau_screening}
 
 
 def lrtei_plan_status(plan: int):
@@ -303,12 +321,13 @@ def lrtei_version() -> str:
 class Plan:
     """A basis plus a plan on the current CUDA device (owns both handles)."""
 
-    def __init__(self, mol, precision: str = "fp64", stream=None, n=None, P=None, omega=None):
+    def __init__(self, mol, precision: str = "fp64", stream=None, n=None, P=None, omega=None,
+                 tau_screening: float = 0.0):
         import torch
         centers, ls, nprim, exps, coefs = mol.packed()
         self.basis = lrtei_basis_create(centers, ls, nprim, exps, coefs)
-        self.plan = lrtei_plan_create(self.basis, omega or mol.omega, n or mol.n, P or mol.P, mol.box_lo, mol.box_hi,
-                                      PRECISIONS[precision], stream)
+        self.plan = lrtei_plan_create_ex(self.basis, omega or mol.omega, n or mol.n, P or mol.P, mol.box_lo,
+                                         mol.box_hi, PRECISIONS[precision], tau_screening, stream)
         self.info = lrtei_plan_info_get(self.plan)
         self.nbf = self.info["nbf"]
         self.npair = self.info["npair"]

@@ -469,3 +469,71 @@ def test_dense_K_matches_oracle_factors(lib, n, P):
     if n3 <= 2000:
         assert np.allclose(got, got.T, rtol=0, atol=1e-12 * np.abs(ref_oracle).max())
     pl.close()
+
+
+def _kept_primitive_pairs(m, tau):
+    """Per unique pair (mu <= nu), the kept primitive pairs (j1, j2) under the screening criterion
+    of Section 6, exp(-a b / (a + b) |A - B|^2) <= tau discards, evaluated here from the shells."""
+    import math
+    shell_of = [s for s, sh in enumerate(m.shells) for _ in range(sh.ncart)]
+    out = []
+    for mu in range(len(shell_of)):
+        for nu in range(mu, len(shell_of)):
+            A, B = m.shells[shell_of[mu]], m.shells[shell_of[nu]]
+            d2 = sum((A.center[l] - B.center[l]) ** 2 for l in range(3))
+            out.append([(j1, j2) for j1, a in enumerate(A.exps) for j2, b in enumerate(B.exps)
+                        if not (tau > 0 and math.exp(-(a * b / (a + b)) * d2) <= tau)])
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_f16"])
+def test_screening_matches_screened_oracle(lib, precision):
+    """Primitive-pair screening (Section 6) with tau = 1e-3 on the contracted s/p/d instance: the
+    plan keeps exactly the primitive pairs the criterion keeps (counted here from the shells), the
+    moments of the kept rows are the oracle's for those primitive pairs, and B and a J-build match
+    the screened oracle within the precision's bound; tau = 0 changes nothing."""
+    import torch
+    m = mol_spd_small()
+    tau = 1e-3
+    kept = _kept_primitive_pairs(m, tau)
+    nkept = sum(len(k) for k in kept)
+    nall = sum(len(k) for k in _kept_primitive_pairs(m, 0.0))
+    assert 0 < nkept < nall
+    o = oracle.Oracle.from_molecule(m, tau_screening=tau)
+    ref = o.assemble_B()
+    ref0 = oracle.Oracle.from_molecule(m).assemble_B()
+    assert rel_fro(ref, ref0) > 1e-9  # screening changes B at this tau
+    pl = lib.Plan(m, precision, tau_screening=tau)
+    assert pl.info["nrows"] == nkept and pl.info["tau_screening"] == tau
+    tol = 1e-13 if precision == "fp64" else 1e-7
+    B = pl.assemble_B().cpu().numpy()
+    pl.status()
+    err = rel_fro(B, ref)
+    D = synth.random_densities(17, m.nbf, 5)
+    J = pl.jbuild(torch.as_tensor(D, device="cuda")).cpu().numpy()
+    errJ = rel_fro(J, o.jbuild_factored(D))
+    print(f"screening tau={tau} {precision}: rows {nkept}/{nall}, B {err:.2e}, J {errJ:.2e}")
+    assert err <= tol and errJ <= tol
+    if precision == "fp64":
+        S = pl.factors()[0].cpu().numpy()
+        shell_of = [s for s, sh in enumerate(m.shells) for _ in range(sh.ncart)]
+        row, nbf = 0, m.nbf
+        for r, (mu, nu) in enumerate((mu, nu) for mu in range(nbf) for nu in range(mu, nbf)):
+            Kn = m.shells[shell_of[nu]].exps.size
+            for d in range(3):
+                if not kept[r]:
+                    continue
+                W = o.moments(mu, nu, d)
+                want = np.array([W[j1 * Kn + j2] for j1, j2 in kept[r]])
+                got = S[d, row:row + len(kept[r])]
+                scale = np.abs(want).max(axis=1, keepdims=True)
+                assert np.all(np.abs(got - want) <= 1e-13 * scale + 1e-300), (mu, nu, d)
+            row += len(kept[r])
+        assert row == S.shape[1]
+        p0 = lib.Plan(m, precision, tau_screening=0.0)
+        pd = lib.Plan(m, precision)
+        assert p0.info["nrows"] == pd.info["nrows"] == nall
+        assert np.array_equal(p0.assemble_B().cpu().numpy(), pd.assemble_B().cpu().numpy())
+        p0.close()
+        pd.close()
+    pl.close()

@@ -20,11 +20,11 @@ pytestmark = pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarn
 
 
 def small_mol(ls=(0, 0), nprim=(1, 1), exps=(0.8, 1.5), coefs=(1.0, 1.0),
-              centers=((0.0, 0.0, 0.0), (1.1, 0.4, -0.7)), omega=0.3, n=32, P=24, box=None):
+              centers=((0.0, 0.0, 0.0), (1.1, 0.4, -0.7)), omega=0.3, n=32, P=24, box=None, tau=0.0):
     c = np.array(centers, dtype=np.float64)
-    kw = {}
+    kw = {"tau_screening": tau}
     if box is not None:
-        kw = dict(box_lo=box[0], box_hi=box[1])
+        kw.update(box_lo=box[0], box_hi=box[1])
     return oracle.Oracle(c, np.array(ls, np.int32), np.array(nprim, np.int32), np.array(exps, np.float64),
                          np.array(coefs, np.float64), omega, n, P, **kw)
 
@@ -309,3 +309,64 @@ def test_axis_permutation():
         a = o1.entry(*q)
         b = o2.entry(*[perm[i] for i in q])
         assert abs(a - b) <= 1e-14 * max(abs(a), 1e-300) + 1e-18
+
+
+# ------------------------------------------------- screening (Section 6, compression) ----
+
+def _screened(a, A, b, B, tau):
+    """The screening criterion of Section 6 for one primitive pair, written out here:
+    exp(-a b / (a + b) |A - B|^2) <= tau."""
+    d2 = sum((A[l] - B[l]) ** 2 for l in range(3))
+    return tau > 0 and math.exp(-(a * b / (a + b)) * d2) <= tau
+
+
+def test_screening_discards_exactly_the_far_pair():
+    """Two one-primitive s functions 4 bohr apart, exponents 2 and 3: overlap factor
+    exp(-1.2 * 16) = 4.6e-9.  Above that tau, screening removes the pair's only term: every entry
+    with (0,1) or (1,0) in either slot is exactly 0 and every other entry is unchanged bit for
+    bit; below it, or with tau = 0, nothing changes."""
+    kw = dict(ls=(0, 0), nprim=(1, 1), exps=(2.0, 3.0), coefs=(1.0, 1.0),
+              centers=((0.0, 0.0, 0.0), (4.0, 0.0, 0.0)), omega=0.4, n=16, P=16)
+    B0 = small_mol(**kw).assemble_B(threads=1)
+    cross = [1, 2]  # rows / columns mu * 2 + nu of the pairs (0, 1) and (1, 0)
+    keep = [0, 3]
+    assert np.all(B0[np.ix_(cross, cross)] != 0.0)
+    for tau, discard in ((1e-8, True), (1e-9, False), (0.0, False)):
+        B = small_mol(tau=tau, **kw).assemble_B(threads=1)
+        assert np.array_equal(B[np.ix_(keep, keep)], B0[np.ix_(keep, keep)])
+        if discard:
+            assert np.all(B[cross, :] == 0.0) and np.all(B[:, cross] == 0.0)
+        else:
+            assert np.array_equal(B, B0)
+
+
+def test_screening_contracted_matches_closed_form_over_kept_pairs():
+    """Contracted s functions with a spread of exponents, tau = 1e-3: some primitive pairs of
+    distinct centres are discarded.  Every entry equals the erf-Boys closed form summed over the
+    kept primitive pairs only (the criterion evaluated here, independently of the oracle)."""
+    centers = ((0.0, 0.0, 0.0), (1.6, 0.4, -0.7), (-0.6, 1.2, 0.5))
+    raw = [((0.8, 6.0), (0.7, 0.3)), ((1.5, 9.0), (1.0, 0.4)), ((1.1, 3.0), (0.5, 0.5))]
+    tau, omega = 1e-3, 0.3
+    o = small_mol(ls=(0, 0, 0), nprim=(2, 2, 2), exps=tuple(e for r in raw for e in r[0]),
+                  coefs=tuple(c for r in raw for c in r[1]), centers=centers, omega=omega, n=32, P=24, tau=tau)
+    bf = [(centers[i], (0, 0, 0), raw[i][0], raw[i][1]) for i in range(3)]
+    flags = [_screened(a, centers[i], b, centers[j], tau) for i in range(3) for j in range(3)
+             for a in raw[i][0] for b in raw[j][0]]
+    assert any(flags) and not all(flags)
+
+    def screened_entry(bf4):
+        cs = [cf.contracted_coefs(e, c, pw) for (_, pw, e, c) in bf4]
+        total = 0.0
+        for ks in itertools.product(*[range(len(b[2])) for b in bf4]):
+            ex = [bf4[f][2][ks[f]] for f in range(4)]
+            if _screened(ex[0], bf4[0][0], ex[1], bf4[1][0], tau) or _screened(ex[2], bf4[2][0], ex[3], bf4[3][0], tau):
+                continue
+            coef = 1.0
+            for f in range(4):
+                coef *= cs[f][ks[f]]
+            total += coef * cf.cart_erf(ex, [bf4[f][0] for f in range(4)], [bf4[f][1] for f in range(4)], omega)
+        return total
+
+    for q in itertools.product(range(3), repeat=4):
+        ref = screened_entry([bf[i] for i in q])
+        assert abs(o.entry(*q) - ref) <= 1e-12 * abs(ref), q
