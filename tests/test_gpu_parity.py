@@ -527,7 +527,8 @@ def test_screening_matches_screened_oracle(lib, precision):
                 want = np.array([W[j1 * Kn + j2] for j1, j2 in kept[r]])
                 got = S[d, row:row + len(kept[r])]
                 scale = np.abs(want).max(axis=1, keepdims=True)
-                assert np.all(np.abs(got - want) <= 1e-13 * scale + 1e-300), (mu, nu, d)
+                # the two quadratures agree to 1e-13 of the row maximum, near-zero moments to rounding
+                assert np.all(np.abs(got - want) <= 1e-13 * scale + 1e-15), (mu, nu, d)
             row += len(kept[r])
         assert row == S.shape[1]
         p0 = lib.Plan(m, precision, tau_screening=0.0)
