@@ -370,3 +370,61 @@ def test_screening_contracted_matches_closed_form_over_kept_pairs():
     for q in itertools.product(range(3), repeat=4):
         ref = screened_entry([bf[i] for i in q])
         assert abs(o.entry(*q) - ref) <= 1e-12 * abs(ref), q
+
+
+# ------------------------------------- Khatri-Rao low-rank compression (Section 6) ----
+
+def _kr_mol():
+    m = synth.random_molecule(4101, natoms=2, cube=3.0, nprim=2, alpha_range=(0.2, 20.0), omega=0.4, n=8, P=8)
+    return oracle.Oracle.from_molecule(m)
+
+
+def test_khatri_rao_full_rank_is_the_factored_form():
+    """With R_d = n the compressed form (eq. approxepsilon) is the factored form: it reproduces
+    Algorithm 1's B (the oracle's assemble_B) to rounding."""
+    from oracle import kr
+    o = _kr_mol()
+    B = o.assemble_B(threads=1)
+    Bk = kr.compressed_B(o, (o.n, o.n, o.n))
+    assert np.linalg.norm(Bk - B) <= 1e-12 * np.linalg.norm(B)
+
+
+@pytest.mark.parametrize("ranks", [(6, 6, 6), (5, 7, 4), (3, 3, 3)])
+def test_khatri_rao_truncation_is_a_projection_of_the_factored_form(ranks):
+    """Truncated ranks: U^(d) = W~^(d) V^(d), so the compressed F_u is F_u (x)_d V^(d) V^(d)T and
+    B_KR = (omega / sqrt(pi)) F Pi K Pi F^T with Pi = (x)_d V V^T and K = sum_p w_p (x)_d A_d^(p).
+    Checked against that product built from the C oracle's F_u (factor_M) and its factors, a route
+    that shares nothing with the compressed one but the SVD; the error shrinks as the ranks grow."""
+    from oracle import kr
+    o = _kr_mol()
+    n = o.n
+    S, _, _ = kr.moment_rows(o)
+    V = [kr.truncated_factors(S[d], ranks[d])[1] for d in range(3)]
+    Pi = np.kron(V[0] @ V[0].T, np.kron(V[1] @ V[1].T, V[2] @ V[2].T))
+    _, w = o.nodes()
+    K = sum(w[p] * np.kron(o.cheb(0, p), np.kron(o.cheb(1, p), o.cheb(2, p))) for p in range(o.P))
+    M = o.factor_M(threads=1)  # rows mu N_b + nu, n^3 columns
+    ref = o.omega / np.sqrt(np.pi) * M @ Pi @ K @ Pi @ M.T
+    Bk = kr.compressed_B(o, ranks)
+    assert np.linalg.norm(Bk - ref) <= 1e-12 * np.linalg.norm(ref)
+    B = o.assemble_B(threads=1)
+    e_trunc = np.linalg.norm(Bk - B) / np.linalg.norm(B)
+    e_more = np.linalg.norm(kr.compressed_B(o, tuple(min(n, r + 1) for r in ranks)) - B) / np.linalg.norm(B)
+    assert 0 < e_more < e_trunc
+
+
+def test_khatri_rao_pin_catches_a_planted_mistake(monkeypatch):
+    """The projection pin above fails when U^(d) loses its singular values (u instead of u sigma),
+    a plausible slip in eq. SVD."""
+    from oracle import kr
+    o = _kr_mol()
+    ranks = (6, 6, 6)
+    good = kr.compressed_B(o, ranks)
+
+    def no_sigma(S, rank):
+        u, sv, vt = np.linalg.svd(S, full_matrices=False)
+        return u[:, :rank], vt[:rank].T, sv
+
+    monkeypatch.setattr(kr, "truncated_factors", no_sigma)
+    bad = kr.compressed_B(o, ranks)
+    assert np.linalg.norm(bad - good) > 1e-3 * np.linalg.norm(good)
