@@ -428,3 +428,51 @@ def test_khatri_rao_pin_catches_a_planted_mistake(monkeypatch):
     monkeypatch.setattr(kr, "truncated_factors", no_sigma)
     bad = kr.compressed_B(o, ranks)
     assert np.linalg.norm(bad - good) > 1e-3 * np.linalg.norm(good)
+
+
+# ------------------------------------------ long-range exchange (appendix, eq. exchange) ----
+
+def test_exchange_factored_equals_direct():
+    """The appendix's factored exchange (through M and the node sum K) equals eq. exchange
+    evaluated on Algorithm 1's B, for three orbitals of a contracted s/p/d molecule."""
+    from oracle import exchange
+    m = synth.random_molecule(4102, natoms=2, cube=3.0, nprim=2, alpha_range=(0.2, 20.0), omega=0.4, n=8, P=8)
+    o = oracle.Oracle.from_molecule(m)
+    Q = np.random.default_rng(5).standard_normal((3, o.nbf))
+    Kd = exchange.exchange_direct(o, Q, threads=1)
+    Kf = exchange.exchange_factored(o, Q, threads=1)
+    assert np.linalg.norm(Kf - Kd) <= 1e-12 * np.linalg.norm(Kd)
+    assert np.allclose(Kd, Kd.T, rtol=0, atol=1e-14 * np.abs(Kd).max())
+
+
+def test_exchange_matches_closed_form_contracted_s():
+    """Contracted s functions, two orbitals: eq. exchange against the erf-Boys closed forms,
+    K(mu, nu) = 2 sum_j sum_{lambda, kappa} q_{j lambda} q_{j kappa} (mu lambda | kappa nu)."""
+    from oracle import exchange
+    centers = ((0.0, 0.0, 0.0), (1.1, 0.4, -0.7), (-0.6, 0.9, 0.5))
+    raw = [((0.8, 2.0), (0.7, 0.3)), ((1.5,), (1.0,)), ((1.1, 3.0), (0.5, 0.5))]
+    o = small_mol(ls=(0, 0, 0), nprim=(2, 1, 2), exps=(0.8, 2.0, 1.5, 1.1, 3.0), coefs=(0.7, 0.3, 1.0, 0.5, 0.5),
+                  centers=centers, omega=0.3, n=32, P=24)
+    bf = [(centers[i], (0, 0, 0), raw[i][0], raw[i][1]) for i in range(3)]
+    Q = np.array([[0.6, -0.3, 0.5], [0.2, 0.8, -0.4]])
+    ints = np.zeros((3, 3, 3, 3))
+    for q in itertools.product(range(3), repeat=4):
+        ints[q] = cf.contracted_entry([bf[i] for i in q], 0.3)
+    ref = np.zeros((3, 3))
+    for mu, nu in itertools.product(range(3), repeat=2):
+        ref[mu, nu] = 2.0 * sum(Q[j, l] * Q[j, k] * ints[mu, l, k, nu] for j in range(2) for l in range(3)
+                                for k in range(3))
+    got = exchange.exchange_direct(o, Q, threads=1)
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+def test_exchange_single_function_is_twice_J():
+    """One basis function, one orbital q: K = 2 q q B(00,00) and J(D = q^2) = q^2 B(00,00), so
+    K = 2 J (the factor 2 and the orbital sum of eq. exchange)."""
+    from oracle import exchange
+    o = small_mol(ls=(0,), nprim=(2,), exps=(0.9, 2.5), coefs=(0.6, 0.5), centers=((0.2, -0.1, 0.3),),
+                  omega=0.4, n=16, P=16)
+    q = 0.7
+    K = exchange.exchange_factored(o, np.array([[q]]), threads=1)
+    J = o.jbuild_factored(np.array([[[q * q]]]), threads=1)
+    assert abs(K[0, 0] - 2.0 * J.reshape(-1)[0]) <= 1e-14 * abs(K[0, 0])
