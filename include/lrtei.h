@@ -24,8 +24,11 @@
  *     stream).  Device pointers (d_*) are owned by the caller; the library owns plans and their
  *     workspaces.  Inputs are validated on the host before anything is launched; a failed
  *     call returns a status and leaves a message for lrtei_last_error().  Device-side failures
- *     (a bounded wait that gave up, a non-finite value) are latched in the plan and reported by
- *     lrtei_plan_status(), which synchronises the plan's stream.
+ *     are latched in the plan's status word (the first one wins) and reported by
+ *     lrtei_plan_status(), which synchronises the device: a bounded wait of the tensor-core
+ *     GEMM that gave up (LRTEI_ERR_TIMEOUT), a NaN or infinity stored into B, J or an entries
+ *     output (LRTEI_ERR_NUMERIC; checked by a warp vote in the kernels that write them), and a
+ *     basis-function index outside [0, N_b) in a device index list (LRTEI_ERR_ARG).
  *   - No call falls back to the CPU: without a usable CUDA device every call that computes
  *     returns LRTEI_ERR_CUDA.
  */
@@ -138,7 +141,9 @@ lrtei_status lrtei_assemble_Bu_rows(lrtei_plan* plan, lrtei_form form, int64_t r
                                     double* d_Bu, int64_t ld, void* stream);
 
 /* ---- entries (Algorithm 1) ---------------------------------------------------------------
- * d_idx4: device int32[4*count] of (mu, nu, ka, la); d_out: device double[count]. */
+ * d_idx4: device int32[4*count] of (mu, nu, ka, la); d_out: device double[count].  The indices
+ * are checked on the device: an entry with an index outside [0, N_b) reads nothing, comes out
+ * as NaN, and lrtei_plan_status then returns LRTEI_ERR_ARG. */
 lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out, void* stream);
 
 /* ---- entries without device allocation ---------------------------------------------------
@@ -150,7 +155,10 @@ lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t coun
  * library is loaded: at most 262144 entries per call (more returns LRTEI_ERR_UNSUPPORTED).  All
  * calls on a device share the array, so calls whose kernels overlap on the GPU race.  The
  * first call on a device performs a one-time lookup of the array's address with that device
- * current; make that first call before any stream capture begins. */
+ * current; make that first call before any stream capture begins.  That address is cached for
+ * the life of the process: calls after a device reset (cudaDeviceReset, or a primary context
+ * released and created again) are not supported.  Out-of-range indices are handled as in
+ * lrtei_entries. */
 lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out,
                                    void* stream);
 
@@ -219,7 +227,10 @@ lrtei_status lrtei_selector_set_params(lrtei_selector* sel, const float* h_param
  * launch of its main kernels ("tc_gemm", "gemm_fp64", "gemm_fp32", "hadamard", "kron",
  * "expand_B", "moments", "build_F", "build_K", "split", "jbuild", "batched" for a replayed
  * J-build graph).  lrtei_profile_get synchronises those
- * events and returns the summed device time and the launch count of one kernel name.
+ * events and returns the summed device time and the launch count of one kernel name.  Two
+ * names are counters rather than kernels: "*" gives the number of kernels the library launched
+ * since the last reset (time 0), and "alloc" the number of device allocations (cudaMalloc and
+ * stream-ordered cudaMallocAsync) it has requested since it was loaded (time 0; never reset).
  * Off by default; process-wide; not thread-safe against concurrent enable/reset. */
 lrtei_status lrtei_profile_enable(int on);
 lrtei_status lrtei_profile_get(const char* kernel, double* total_ms, int64_t* launches);

@@ -196,6 +196,7 @@ cudaError_t launch_build_K(int n, int P, const double* d_C, const double* d_w, d
                            cudaStream_t st) {
   const int nn = n * n;
   Pair32* zp = nullptr;
+  count_alloc();
   cudaError_t e = cudaMallocAsync((void**)&zp, sizeof(Pair32) * (size_t)nn * P, st);
   if (e != cudaSuccess) return e;
   count_launch();
@@ -269,44 +270,52 @@ void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const
 
 // One block per unique pair r = (mu, nu); writes full rows mu*N_b+nu and nu*N_b+mu.
 __global__ void k_expand_B(int nbf, const double* __restrict__ Bu, int64_t ldu, double scale, double* __restrict__ B,
-                           int64_t ldB, const int* __restrict__ pair_mu, const int* __restrict__ pair_nu) {
+                           int64_t ldB, const int* __restrict__ pair_mu, const int* __restrict__ pair_nu, int* status) {
   const int64_t r = blockIdx.x;
   const int mu = pair_mu[r], nu = pair_nu[r];
   const double* src = Bu + (size_t)r * ldu;
   double* row1 = B + ((size_t)mu * nbf + nu) * ldB;
   double* row2 = B + ((size_t)nu * nbf + mu) * ldB;
   const int64_t nc = (int64_t)nbf * nbf;
+  bool bad = false;
   for (int64_t col = threadIdx.x; col < nc; col += blockDim.x) {
     const int ka = (int)(col / nbf), la = (int)(col % nbf);
     const double v = scale * src[pair_idx(nbf, ka, la)];
+    bad |= !isfinite(v);
     row1[col] = v;
     if (mu != nu) row2[col] = v;
   }
+  latch_nonfinite_warp(status, bad);
 }
 
 void launch_expand_B(const PairTable& t, int nbf, const double* d_Bu, int64_t ldu, double scale, double* d_B,
-                     int64_t ldB, cudaStream_t st) {
+                     int64_t ldB, int* d_status, cudaStream_t st) {
   count_launch();
-  k_expand_B<<<(unsigned)t.npair, 256, 0, st>>>(nbf, d_Bu, ldu, scale, d_B, ldB, t.pair_mu, t.pair_nu);
+  k_expand_B<<<(unsigned)t.npair, 256, 0, st>>>(nbf, d_Bu, ldu, scale, d_B, ldB, t.pair_mu, t.pair_nu, d_status);
 }
 
 // One block per row R = a N_b + b of B: out row R - R0 = B_u row pair(a, b) over the columns (ka, la).
 __global__ void k_expand_B_rows(int nbf, const double* __restrict__ Bu, int64_t ldu, int64_t R0, double* __restrict__ out,
-                                int64_t ldo) {
+                                int64_t ldo, int* status) {
   const int64_t R = R0 + blockIdx.x;
   const int a = (int)(R / nbf), b = (int)(R % nbf);
   const double* src = Bu + (size_t)pair_idx(nbf, a, b) * ldu;
   double* dst = out + (size_t)blockIdx.x * ldo;
   const int64_t nc = (int64_t)nbf * nbf;
-  for (int64_t col = threadIdx.x; col < nc; col += blockDim.x)
-    dst[col] = src[pair_idx(nbf, (int)(col / nbf), (int)(col % nbf))];
+  bool bad = false;
+  for (int64_t col = threadIdx.x; col < nc; col += blockDim.x) {
+    const double v = src[pair_idx(nbf, (int)(col / nbf), (int)(col % nbf))];
+    bad |= !isfinite(v);
+    dst[col] = v;
+  }
+  latch_nonfinite_warp(status, bad);
 }
 
 void launch_expand_B_rows(int nbf, const double* d_Bu, int64_t ldu, int64_t R0, int64_t R1, double* d_out, int64_t ldo,
-                          cudaStream_t st) {
+                          int* d_status, cudaStream_t st) {
   if (R1 <= R0) return;
   count_launch();
-  k_expand_B_rows<<<(unsigned)(R1 - R0), 256, 0, st>>>(nbf, d_Bu, ldu, R0, d_out, ldo);
+  k_expand_B_rows<<<(unsigned)(R1 - R0), 256, 0, st>>>(nbf, d_Bu, ldu, R0, d_out, ldo, d_status);
 }
 
 // d_u[r][q] = D_q(mu, nu) * (mu == nu ? 1 : 2); D stored R x N_b x N_b.
@@ -337,21 +346,26 @@ void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStr
 }
 
 // J_q(mu, nu) = J_q(nu, mu) = scale * Ju[r][q].
-__global__ void k_unpack_J(int nbf, int R, const double* __restrict__ Ju, double scale, double* __restrict__ J) {
+__global__ void k_unpack_J(int nbf, int R, const double* __restrict__ Ju, double scale, double* __restrict__ J,
+                           int* status) {
   const int64_t total = (int64_t)R * nbf * nbf;
+  bool bad = false;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(t / ((int64_t)nbf * nbf));
     const int mu = (int)((t / nbf) % nbf), nu = (int)(t % nbf);
-    J[t] = scale * Ju[pair_idx(nbf, mu, nu) * R + q];
+    const double v = scale * Ju[pair_idx(nbf, mu, nu) * R + q];
+    bad |= !isfinite(v);
+    J[t] = v;
   }
+  latch_nonfinite_warp(status, bad);
 }
 
-void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, cudaStream_t st) {
+void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, int* d_status, cudaStream_t st) {
   const int64_t total = (int64_t)R * nbf * nbf;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   count_launch();
-  k_unpack_J<<<(unsigned)blocks, 256, 0, st>>>(nbf, R, d_Ju, scale, d_J);
+  k_unpack_J<<<(unsigned)blocks, 256, 0, st>>>(nbf, R, d_Ju, scale, d_J, d_status);
 }
 
 }  // namespace lrtei

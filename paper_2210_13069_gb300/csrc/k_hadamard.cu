@@ -1,8 +1,8 @@
 // k_hadamard.cu -- FP64 CUDA-core form of Theorem 1 / Algorithm 1 (entry-wise Hadamard form):
 //   B_u(r, c) = (w/sqrt(pi)) sum_p w_p sum_{j in r} sum_{j' in c} c_j c_j' prod_d (T_{d,p}(j,:) . S_d(j',:))
 // with T_{d,p} = S_d A_d^(p) computed once per plan.  The sum over the quadrature nodes is
-// Neumaier-compensated in FP64.  This is the plain FP64 reference form of the device path; the
-// tensor-core form of the same contraction is in k_tcgen05.cu.
+// Neumaier-compensated in FP64.  This is the FP64 CUDA-core form of the contraction; the tensor-core
+// path (k_tcgen05.cu) runs the Khatri-Rao factored form of the same B instead.
 #include "lrtei_internal.h"
 
 namespace lrtei {
@@ -64,9 +64,25 @@ __device__ double hadamard_entry(int64_t r, int64_t c, int n, int P, int64_t nro
 
 __global__ void k_hadamard_pairs(int n, int P, int64_t nrows, const int64_t* pair_row, const double* row_c,
                                  const double* S, const double* T, const double* w, double pref, const int64_t* rr,
-                                 const int64_t* cc, int64_t count, double* out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = pref * hadamard_entry(rr[e], cc[e], n, P, nrows, pair_row, row_c, S, T, w);
+                                 const int64_t* cc, int64_t count, double* out, int* status) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // every thread of the block runs the same number of iterations, so the warp vote is convergent
+  const int64_t iters = (count + stride - 1) / stride;
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t e = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < count) {
+      const int64_t r = rr[e], c = cc[e];
+      if (r < 0 || c < 0) {
+        out[e] = __longlong_as_double(0x7FF8000000000000LL);  // an index outside the basis
+      } else {
+        const double v = pref * hadamard_entry(r, c, n, P, nrows, pair_row, row_c, S, T, w);
+        bad |= !isfinite(v);
+        out[e] = v;
+      }
+    }
+  }
+  latch_nonfinite_warp(status, bad);
 }
 
 // Few entries: one warp per entry, the lanes share the quadrature nodes (p = lane, lane + 32, ...)
@@ -74,11 +90,16 @@ __global__ void k_hadamard_pairs(int n, int P, int64_t nrows, const int64_t* pai
 __global__ void k_hadamard_pairs_warp(int n, int P, int64_t nrows, const int64_t* __restrict__ pair_row,
                                       const double* __restrict__ row_c, const double* __restrict__ S,
                                       const double* __restrict__ T, const double* __restrict__ w, double pref,
-                                      const int64_t* rr, const int64_t* cc, int64_t count, double* out) {
+                                      const int64_t* rr, const int64_t* cc, int64_t count, double* out,
+                                      int* status) {
   const int lane = threadIdx.x & 31;
   const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (e >= count) return;
+  if (e >= count) return;  // whole warps: e is uniform across the warp
   const int64_t r = rr[e], c = cc[e];
+  if (r < 0 || c < 0) {  // an index outside the basis
+    if (lane == 0) out[e] = __longlong_as_double(0x7FF8000000000000LL);
+    return;
+  }
   const int64_t j0 = pair_row[r], j1 = pair_row[r + 1], k0 = pair_row[c], k1 = pair_row[c + 1];
   double s = 0.0;
   for (int p = lane; p < P; p += 32) {
@@ -98,24 +119,27 @@ __global__ void k_hadamard_pairs_warp(int n, int P, int64_t nrows, const int64_t
     s += w[p] * acc;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[e] = pref * s;
+  if (lane == 0) {
+    out[e] = pref * s;
+    if (!isfinite(pref * s)) latch_status(status, (int)kDevNonFinite);
+  }
 }
 
 void launch_hadamard_pairs(const PairTable& t, int n, int P, const double* d_S, const double* d_T,
                            const double* d_w, double pref, const int64_t* d_r, const int64_t* d_c, int64_t count,
-                           double* d_out, cudaStream_t st) {
+                           double* d_out, int* d_status, cudaStream_t st) {
   if (count <= 0) return;
   count_launch();
   if (count < 152 * 128) {  // too few entries to fill the GPU one thread each
     const int64_t threads = count * 32;
     k_hadamard_pairs_warp<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, P, t.nrows, t.pair_row, t.row_c, d_S,
-                                                                            d_T, d_w, pref, d_r, d_c, count, d_out);
+                                                                            d_T, d_w, pref, d_r, d_c, count, d_out, d_status);
     return;
   }
   int blocks = (int)((count + 127) / 128);
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_hadamard_pairs<<<blocks, 128, 0, st>>>(n, P, t.nrows, t.pair_row, t.row_c, d_S, d_T, d_w, pref, d_r, d_c, count,
-                                          d_out);
+                                          d_out, d_status);
 }
 
 // Rows [r0, r1) of B_u, all npair columns; blockIdx.y = row, threads over columns.
@@ -143,25 +167,25 @@ void launch_hadamard_rows(const PairTable& t, int n, int P, const double* d_S, c
   }
 }
 
-__device__ __forceinline__ int64_t pair_index(int nbf, int a, int b) {
-  const int lo = a < b ? a : b, hi = a < b ? b : a;
-  return (int64_t)lo * nbf - (int64_t)lo * (lo - 1) / 2 + (hi - lo);
-}
-
-__global__ void k_idx4_to_pairs(int nbf, const int32_t* idx4, int64_t count, int64_t* r, int64_t* c) {
+// The caller's indices are checked here, on the device: an index outside [0, nbf) gives the pair
+// -1 (the entry kernels then write NaN and read nothing) and latches kDevBadIndex.
+__global__ void k_idx4_to_pairs(int nbf, const int32_t* idx4, int64_t count, int64_t* r, int64_t* c, int* status) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    r[e] = pair_index(nbf, idx4[4 * e], idx4[4 * e + 1]);
-    c[e] = pair_index(nbf, idx4[4 * e + 2], idx4[4 * e + 3]);
+    const int64_t pr = checked_pair_index(nbf, idx4[4 * e], idx4[4 * e + 1]);
+    const int64_t pc = checked_pair_index(nbf, idx4[4 * e + 2], idx4[4 * e + 3]);
+    if (pr < 0 || pc < 0) latch_status(status, (int)kDevBadIndex);
+    r[e] = pr < 0 || pc < 0 ? -1 : pr;
+    c[e] = pr < 0 || pc < 0 ? -1 : pc;
   }
 }
 
-void launch_idx4_to_pairs(int nbf, const int32_t* d_idx4, int64_t count, int64_t* d_r, int64_t* d_c,
+void launch_idx4_to_pairs(int nbf, const int32_t* d_idx4, int64_t count, int64_t* d_r, int64_t* d_c, int* d_status,
                           cudaStream_t st) {
   if (count <= 0) return;
   int blocks = (int)((count + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   count_launch();
-  k_idx4_to_pairs<<<blocks, 256, 0, st>>>(nbf, d_idx4, count, d_r, d_c);
+  k_idx4_to_pairs<<<blocks, 256, 0, st>>>(nbf, d_idx4, count, d_r, d_c, d_status);
 }
 
 }  // namespace lrtei

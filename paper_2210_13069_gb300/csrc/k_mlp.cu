@@ -196,6 +196,7 @@ lrtei_status lrtei_selector_create(int hidden, uint64_t seed, lrtei_selector** o
   fill(o.w2, hidden * hidden, hidden);
   fill(o.w3, mlp::kOut * hidden, hidden);
   cudaError_t e;
+  for (int k = 0; k < 5; ++k) count_alloc();
   if ((e = cudaMalloc(&s->d_params, sizeof(float) * s->np)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_m, sizeof(float) * s->np)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_v, sizeof(float) * s->np)) != cudaSuccess ||
@@ -265,6 +266,7 @@ lrtei_status lrtei_selector_train_epoch(lrtei_selector* s, const float* d_X, con
   if (s->idx_cap < N) {
     cudaFree(s->d_idx);
     s->d_idx = nullptr;
+    count_alloc();
     LRTEI_CUDA(cudaMalloc(&s->d_idx, sizeof(int) * N));
     s->idx_cap = N;
   }

@@ -83,6 +83,8 @@ struct Params {
   int* status;
   int64_t a_row0;         // row of C that row 0 of A computes (a row band of a symmetric product)
   int64_t blk0, blk1;     // symmetric product: the 128-row blocks [blk0, blk1) of the upper triangle
+  long long test_stall;   // > 0 (tests only): the MMA thread first waits this many cycles on a barrier
+                          // that nothing completes, so that the bounded-wait failure path runs
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -117,14 +119,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait: false if the CTA is aborting or the wait gave up (which raises the abort).
 // sleep_ns > 0 parks the waiting warp between polls, leaving issue slots to the MMA thread.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                          unsigned sleep_ns = 0) {
+                                          unsigned sleep_ns = 0, long long limit = kWaitCycles) {
   long long t0 = clock64();
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
     if (sleep_ns) __nanosleep(sleep_ns);
     if ((++spins & 255u) == 0) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit) {
         *abort_flag = 1;
         atomicExch(status, (int)kDevTimeout);
         return false;
@@ -363,7 +365,8 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
   uint64_t* acce = accf + 2;         // [2] accumulator buffer drained
   uint64_t* done = acce + 2;         // all MMAs retired
   uint64_t* tstored = done + 1;      // the staged tile was stored: the ring may be refilled
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tstored + 1);
+  uint64_t* never = tstored + 1;     // completed by nobody (the test stall waits on it)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -380,6 +383,7 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
     }
     mbar_init(done, 1);
     mbar_init(tstored, epi_warps<BN>());
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -443,6 +447,8 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
       const uint32_t idesc = instr_desc<BN, PLAIN>();
       uint32_t it = 0, cg = 0;  // k steps and chunks consumed, across items
       bool ok = true;
+      // test hook: a wait that runs out (nothing arrives on `never`), then the abort path
+      if (p.test_stall > 0) ok = mbar_wait(never, 0u, abort_flag, p.status, 0, p.test_stall);
       for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const Work w = work_item<BN>(p, item);
         for (int c = 0; c < w.nchunks && ok; ++c, ++cg) {
@@ -816,6 +822,13 @@ static lrtei_status tc_gemm_impl(const SplitMatrix& A, const SplitMatrix& B, int
   p.status = d_status;
   p.splits = splits;
   p.a_row0 = row0;
+  {
+    // LRTEI_TEST_STALL_CYCLES (tests only): every CTA's MMA thread first waits that many cycles on
+    // a barrier nothing completes, gives up, raises LRTEI_ERR_TIMEOUT and leaves the kernel
+    // through the bounded drain path.
+    const char* v = getenv("LRTEI_TEST_STALL_CYCLES");
+    p.test_stall = (v && *v) ? std::max(0LL, atoll(v)) : 0;
+  }
   // Tile width: the tensor pipe runs at full rate from N = 128 on (a 128 x 64 MMA is bound by
   // its operand reads from shared memory); narrow outputs take narrower tiles.  Plain BF16 keeps
   // 64-column tiles.

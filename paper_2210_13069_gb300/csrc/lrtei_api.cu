@@ -81,6 +81,7 @@ struct lrtei_plan {
     void* q = nullptr;
     size_t b = count * sizeof(T);
     if (b == 0) b = 16;
+    count_alloc();
     cudaError_t e = cudaMalloc(&q, b);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -373,6 +374,7 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
         if (e != cudaSuccess) { delete pl; return cuda_fail(e, what); }
         return LRTEI_OK;
       };
+      for (int k = 0; k < 5; ++k) count_alloc();
       if ((ce = cudaMallocAsync((void**)&d_key, sizeof(int) * 3 * (size_t)t.nrows, st)) != cudaSuccess ||
           (ce = cudaMallocAsync((void**)&d_l, sizeof(int) * (size_t)ns, st)) != cudaSuccess ||
           (ce = cudaMallocAsync((void**)&d_rep, sizeof(int64_t) * (size_t)nkeys, st)) != cudaSuccess ||
@@ -429,6 +431,7 @@ lrtei_status lrtei_plan_status(lrtei_plan* plan) {
   LRTEI_CUDA(cudaMemset(plan->d_status, 0, sizeof(int)));
   if (h == kDevTimeout) { set_error("a device-side bounded wait gave up"); return LRTEI_ERR_TIMEOUT; }
   if (h == kDevNonFinite) { set_error("non-finite value detected on the device"); return LRTEI_ERR_NUMERIC; }
+  if (h == kDevBadIndex) { set_error("an index list held a basis-function index outside [0, N_b)"); return LRTEI_ERR_ARG; }
   return LRTEI_OK;
 }
 
@@ -557,6 +560,7 @@ struct Scratch {
   template <typename T>
   lrtei_status get(T** p, size_t count) {
     void* q = nullptr;
+    count_alloc();
     cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(16, count * sizeof(T)), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -762,7 +766,7 @@ static lrtei_status assemble_B_host_banded(lrtei_plan* pl, double* hB, int64_t l
       if (nchunk >= 2 && (e = cudaStreamWaitEvent(st, copied[slot], 0)) != cudaSuccess) { fail(e, "wait copy"); break; }
       {
         ProfScope ps("expand_B", st);
-        launch_expand_B_rows(nbf, Bu, npair, R, Rn, stage[slot], nb2, st);
+        launch_expand_B_rows(nbf, Bu, npair, R, Rn, stage[slot], nb2, pl->d_status, st);
       }
       if ((status = finish_launch("expand_B_rows")) != LRTEI_OK) break;
       if ((e = cudaEventRecord(ready[slot], st)) != cudaSuccess) { fail(e, "record"); break; }
@@ -1040,7 +1044,7 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
     sub.npair = r1 - r0;
     {
       ProfScope ps("expand_B", st);
-      launch_expand_B(sub, nbf, blk, npair, 1.0, d_B, ld, st);
+      launch_expand_B(sub, nbf, blk, npair, 1.0, d_B, ld, plan->d_status, st);
     }
     LRTEI_TRY(finish_launch("expand_B"));
   }
@@ -1057,9 +1061,9 @@ lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t coun
   int64_t *r, *c;
   LRTEI_TRY(sc.get(&r, count));
   LRTEI_TRY(sc.get(&c, count));
-  launch_idx4_to_pairs(plan->basis.nbf, d_idx4, count, r, c, st);
+  launch_idx4_to_pairs(plan->basis.nbf, d_idx4, count, r, c, plan->d_status, st);
   launch_hadamard_pairs(plan->t, plan->n, plan->P, plan->d_S, plan->d_T, plan->d_w, plan->omega / sqrt(kPi), r, c,
-                        count, d_out, st);
+                        count, d_out, plan->d_status, st);
   return finish_launch("entries");
 }
 
@@ -1124,7 +1128,7 @@ static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double
   }
   // J_u = F Y : npair x R
   LRTEI_TRY(tc_gemm(plan->Fsp, Ysp, npair, R, 1.0, Ju, R, false, false, s3, part, plan->d_status, st));
-  launch_unpack_J(nbf, R, Ju, 1.0, d_J, st);
+  launch_unpack_J(nbf, R, Ju, 1.0, d_J, plan->d_status, st);
   return finish_launch("jbuild (tensor cores)");
 }
 
@@ -1168,7 +1172,7 @@ static lrtei_status jbuild_streamed(lrtei_plan* plan, const double* d_D, int R, 
       ProfScope ps("gemm_fp64", st);
       gemm_cuda_core<double>(false, true, nr, R, n3, 1.0, Fb, n3, Yt, n3, 0.0, Ju + r0 * R, R, st);
     }
-    launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+    launch_unpack_J(nbf, R, Ju, pref, d_J, plan->d_status, st);
     return finish_launch("jbuild (streamed)");
   }
   // tensor cores: X^T blocks (R x n^3) into per-block partials, summed once
@@ -1221,7 +1225,7 @@ static lrtei_status jbuild_streamed(lrtei_plan* plan, const double* d_D, int R, 
     }
     LRTEI_TRY(tc_gemm(A, Ysp, nr, R, 1.0, Ju + r0 * R, R, false, false, splits_for(nr, n3), part, plan->d_status, st));
   }
-  launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+  launch_unpack_J(nbf, R, Ju, pref, d_J, plan->d_status, st);
   return finish_launch("jbuild (streamed, tensor cores)");
 }
 
@@ -1283,7 +1287,7 @@ static lrtei_status jbuild_direct(lrtei_plan* plan, const double* d_D, int R, do
     ProfScope ps("gemm_fp64", st);
     gemm_cuda_core<double>(false, true, npair, R, n3, 1.0, plan->d_F, n3, Yt, n3, 0.0, Ju, R, st);
   }
-  launch_unpack_J(nbf, R, Ju, pref, d_J, st);
+  launch_unpack_J(nbf, R, Ju, pref, d_J, plan->d_status, st);
   return finish_launch("jbuild");
 }
 
@@ -1339,6 +1343,7 @@ lrtei_status plan_view(const lrtei_plan* plan, PlanView* v) {
   v->S = plan->d_S;
   v->C = plan->d_C;
   v->w = plan->d_w;
+  v->status = plan->d_status;
   return LRTEI_OK;
 }
 }  // namespace lrtei

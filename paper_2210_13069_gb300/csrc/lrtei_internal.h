@@ -18,7 +18,25 @@ constexpr int kMomentPanels = 8; // panels of the device moment quadrature
 constexpr int kMomentPts = 32;   // Gauss-Legendre points per panel (one per lane)
 
 // Device-side status word (latched by kernels, read by lrtei_plan_status).
-enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevNonFinite = 2 };
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevNonFinite = 2, kDevBadIndex = 3 };
+
+// Latch a device status code unless one is latched already (the first failure is reported).
+__device__ __forceinline__ void latch_status(int* status, int code) {
+  if (status) atomicCAS(status, (int)kDevOk, code);
+}
+// Warp-wide non-finite flag: every lane of a full warp calls it once with its own flag; one lane
+// latches kDevNonFinite if any lane saw a NaN or an infinity.
+__device__ __forceinline__ void latch_nonfinite_warp(int* status, bool bad) {
+  const unsigned any = __ballot_sync(0xffffffffu, bad);
+  if (any && (threadIdx.x & 31) == 0) latch_status(status, (int)kDevNonFinite);
+}
+// Unique-pair index of (a, b) in the row-major upper triangle of nbf basis functions, or -1 when
+// a or b lies outside [0, nbf) (the caller's index lists are checked on the device).
+__host__ __device__ __forceinline__ int64_t checked_pair_index(int nbf, int a, int b) {
+  if (a < 0 || b < 0 || a >= nbf || b >= nbf) return -1;
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return (int64_t)lo * nbf - (int64_t)lo * (lo - 1) / 2 + (hi - lo);
+}
 
 void set_error(const char* fmt, ...);
 lrtei_status cuda_fail(cudaError_t e, const char* what);
@@ -34,6 +52,9 @@ void count_launch();
 void count_launches(long long n);
 long long launch_count();
 void set_launch_count(long long n);
+// Counts device allocation requests (cudaMalloc / cudaMallocAsync) made by the library
+// (reported by lrtei_profile_get("alloc"); never reset).
+void count_alloc();
 
 // Kernel timing: events recorded on the launching stream when profiling is enabled.
 struct ProfScope {
@@ -100,14 +121,17 @@ void launch_gather_moments(int64_t count, int n, const int* d_key, const double*
 // T[d][p][row][b] = sum_a S[d][row][a] C[d][p][a][b]
 void launch_tmat(int64_t nrows, int n, int P, const double* d_S, const double* d_C, double* d_T, cudaStream_t st);
 // Entries by Algorithm 1 on unique pairs: out[e] = B_u(r_e, c_e), prefactor included.
+// Entries whose r or c is negative (an index outside the basis) come out as NaN; a non-finite
+// result of a valid entry latches kDevNonFinite into *d_status.
 void launch_hadamard_pairs(const PairTable& t, int n, int P, const double* d_S, const double* d_T,
                            const double* d_w, double pref, const int64_t* d_r, const int64_t* d_c, int64_t count,
-                           double* d_out, cudaStream_t st);
+                           double* d_out, int* d_status, cudaStream_t st);
 // Block of B_u rows [r0, r1) x all columns, Hadamard form.
 void launch_hadamard_rows(const PairTable& t, int n, int P, const double* d_S, const double* d_T, const double* d_w,
                           double pref, int64_t r0, int64_t r1, double* d_Bu, int64_t ld, cudaStream_t st);
-// (mu,nu,ka,la) quadruples -> unique pair indices.
-void launch_idx4_to_pairs(int nbf, const int32_t* d_idx4, int64_t count, int64_t* d_r, int64_t* d_c,
+// (mu,nu,ka,la) quadruples -> unique pair indices; an index outside [0, nbf) gives -1 and latches
+// kDevBadIndex into *d_status.
+void launch_idx4_to_pairs(int nbf, const int32_t* d_idx4, int64_t count, int64_t* d_r, int64_t* d_c, int* d_status,
                           cudaStream_t st);
 
 // ---------------------------------------------------------------- factored form
@@ -122,16 +146,18 @@ cudaError_t launch_build_K(int n, int P, const double* d_C, const double* d_w, d
 void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const double* d_X, double* d_Y,
                        int64_t ncol, double* d_t1, double* d_t2, cudaStream_t st);
 // Expand the unique-pair square B_u (npair x npair, ld) into full B (N_b^2 x N_b^2, ldB), times scale.
+// The expansion and unpacking kernels latch kDevNonFinite into *d_status if they store a NaN or an
+// infinity (a warp vote per store loop; no extra memory traffic).
 void launch_expand_B(const PairTable& t, int nbf, const double* d_Bu, int64_t ldu, double scale, double* d_B,
-                     int64_t ldB, cudaStream_t st);
+                     int64_t ldB, int* d_status, cudaStream_t st);
 // Rows [R0, R1) of full B (R = a N_b + b) from complete rows of B_u: out row R - R0 (ldo) is
 // row pair(min(a, b), max(a, b)) of B_u gathered over the columns (ka, la).
 void launch_expand_B_rows(int nbf, const double* d_Bu, int64_t ldu, int64_t R0, int64_t R1, double* d_out, int64_t ldo,
-                          cudaStream_t st);
+                          int* d_status, cudaStream_t st);
 // Densities -> unique-pair vectors: d_u[r][q] = D_q(mu,nu) * (mu == nu ? 1 : 2).
 void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStream_t st);
 // Unique-pair results -> full symmetric J: J_q(mu,nu) = J_q(nu,mu) = scale * Ju[r][q].
-void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, cudaStream_t st);
+void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, int* d_status, cudaStream_t st);
 
 // ---------------------------------------------------------------- CUDA-core GEMM
 // C[M x N] = alpha * op(A) op(B) + beta * C, row-major; transA: A is K x M; transB: B is N x K.
@@ -186,6 +212,7 @@ struct PlanView {
   const double* S;  // 3 x nrows x n moments
   const double* C;  // 3 x P x n x n Chebyshev coefficients
   const double* w;  // P quadrature weights
+  int* status;      // the plan's device status word
 };
 lrtei_status plan_view(const lrtei_plan* plan, PlanView* v);
 

@@ -19,6 +19,11 @@
 //    once, with that device current; make that first call before any stream capture begins.
 //  - It reads only the plan's moments, Chebyshev coefficients and weights, which the plan
 //    computes when it is created, so it never triggers the plan's lazily built tables.
+//  - The array's address is cached per device for the life of the process.  A device reset
+//    (cudaDeviceReset, or a primary context released and created again) reloads the module and
+//    invalidates that address: calls after such a reset are not supported.
+//  - Indices outside [0, N_b) are caught on the device: the entry comes out as NaN, nothing is
+//    read for it, and lrtei_plan_status then returns LRTEI_ERR_ARG.
 #include <mutex>
 
 #include "lrtei_internal.h"
@@ -55,16 +60,15 @@ lrtei_status scratch_address(int64_t** out) {
   return LRTEI_OK;
 }
 
-__device__ __forceinline__ int64_t pair_of(int nbf, int a, int b) {
-  const int lo = a < b ? a : b, hi = a < b ? b : a;
-  return (int64_t)lo * nbf - (int64_t)lo * (lo - 1) / 2 + (hi - lo);
-}
-
+// An index outside [0, nbf) gives the pair -1 and latches kDevBadIndex.
 __global__ void k_noalloc_pairs(int nbf, const int32_t* __restrict__ idx4, int64_t count, int64_t* __restrict__ rc,
-                                int64_t maxe) {
+                                int64_t maxe, int* status) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    rc[e] = pair_of(nbf, idx4[4 * e], idx4[4 * e + 1]);
-    rc[maxe + e] = pair_of(nbf, idx4[4 * e + 2], idx4[4 * e + 3]);
+    const int64_t pr = checked_pair_index(nbf, idx4[4 * e], idx4[4 * e + 1]);
+    const int64_t pc = checked_pair_index(nbf, idx4[4 * e + 2], idx4[4 * e + 3]);
+    if (pr < 0 || pc < 0) latch_status(status, (int)kDevBadIndex);
+    rc[e] = pr < 0 || pc < 0 ? -1 : pr;
+    rc[maxe + e] = pr < 0 || pc < 0 ? -1 : pc;
   }
 }
 
@@ -74,9 +78,13 @@ __global__ void k_noalloc_entries(int n, int P, int64_t nrows, const int64_t* __
                                   const double* __restrict__ row_c, const double* __restrict__ S,
                                   const double* __restrict__ C, const double* __restrict__ w, double pref,
                                   const int64_t* __restrict__ rc, int64_t maxe, int64_t count,
-                                  double* __restrict__ out) {
+                                  double* __restrict__ out, int* status) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = rc[e], c = rc[maxe + e];
+    if (r < 0 || c < 0) {  // an index outside the basis: nothing is read for this entry
+      out[e] = __longlong_as_double(0x7FF8000000000000LL);
+      continue;
+    }
     const int64_t j0 = pair_row[r], j1 = pair_row[r + 1], k0 = pair_row[c], k1 = pair_row[c + 1];
     double s = 0.0, comp = 0.0;
     for (int p = 0; p < P; ++p) {
@@ -104,6 +112,7 @@ __global__ void k_noalloc_entries(int n, int P, int64_t nrows, const int64_t* __
       s = tsum;
     }
     out[e] = pref * (s + comp);
+    if (!isfinite(out[e])) latch_status(status, (int)kDevNonFinite);
   }
 }
 }  // namespace
@@ -132,11 +141,11 @@ extern "C" lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d
   int blocks = (int)((count + 127) / 128);
   if (blocks > 152 * 32) blocks = 152 * 32;
   count_launch();
-  k_noalloc_pairs<<<blocks, 128, 0, st>>>(v.nbf, d_idx4, count, rc, kNoAllocMaxEntries);
+  k_noalloc_pairs<<<blocks, 128, 0, st>>>(v.nbf, d_idx4, count, rc, kNoAllocMaxEntries, v.status);
   count_launch();
   k_noalloc_entries<<<blocks, 128, 0, st>>>(v.n, v.P, v.t->nrows, v.t->pair_row, v.t->row_c, v.S, v.C, v.w,
                                             v.omega / sqrt(3.14159265358979323846), rc, kNoAllocMaxEntries, count,
-                                            d_out);
+                                            d_out, v.status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "lrtei_entries_noalloc launch");
   return LRTEI_OK;

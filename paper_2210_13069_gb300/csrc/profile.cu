@@ -14,6 +14,7 @@ struct Rec {
 };
 std::mutex g_mu;
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};  // device allocations the library has requested (never reset)
 std::vector<Rec> g_recs;
 bool g_on = false;
 }  // namespace
@@ -22,6 +23,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(); }
 void set_launch_count(long long n) { g_launches.store(n); }
+void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), st(s) {
   if (!g_on) return;
@@ -67,6 +69,11 @@ lrtei_status lrtei_profile_get(const char* kernel, double* total_ms, int64_t* la
   if (kernel[0] == '*' && kernel[1] == 0) {  // all launches since the last reset
     *total_ms = 0.0;
     *launches = lrtei::g_launches.load();
+    return LRTEI_OK;
+  }
+  if (std::string(kernel) == "alloc") {  // device allocations requested since the library was loaded
+    *total_ms = 0.0;
+    *launches = lrtei::g_allocs.load();
     return LRTEI_OK;
   }
   std::lock_guard<std::mutex> lk(lrtei::g_mu);
