@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-nb360", action="store_true")
     ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
+    ap.add_argument("--kr-eps", type=float, default=1e-8,
+                    help="Khatri-Rao compression threshold of the compressed-form leg (0: leg off)")
     ap.add_argument("--profile-region", choices=["none", "main", "jbuild"], default="none",
                     help="bracket that leg's timed launches with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ref-seconds", type=float, default=None,
@@ -511,6 +513,12 @@ def run_ours(args, world, rank, local):
             fp64["speedup_jbuilds"] = jb["value"] / fp64["jbuilds_per_s"]
         p64.close()
 
+    # ---- Khatri-Rao low-rank compression (Section 6, eq. approxepsilon) of the same workload; B
+    # holds the uncompressed FP64 B here when the FP64 leg ran
+    kr = None
+    if args.kr_eps > 0 and args.precision in ("split_f16", "split_f16_8", "bf16"):
+        kr = run_kr(args, mol, B, world, have_fp64_B=fp64 is not None)
+
     # ---- the same step with the eight-product scheme (error about seven times smaller)
     split8 = None
     if args.precision == "split_f16" and not args.no_fp64:
@@ -614,7 +622,7 @@ def run_ours(args, world, rank, local):
                        "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
-            "jbuilds": jb, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "jbuilds": jb, "kr_compressed": kr, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)
@@ -622,6 +630,69 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_kr(args, mol, B, world, have_fp64_B=False):
+    """The same step on a Khatri-Rao compressed plan (eq. approxepsilon, singular values kept down
+    to kr_eps of the largest): rank, time per B, entries/s, J-builds/s, and the change of B against
+    the uncompressed FP64 B (in `B` when have_fp64_B)."""
+    import torch
+    from paper_2210_13069_gb300 import lrtei, synth
+    stream = torch.cuda.current_stream()
+    nb2 = mol.nbf * mol.nbf
+    Bref = B.clone() if have_fp64_B and B.numel() * 8 < 12e9 else None
+    pk = lrtei.Plan(mol, args.precision)
+    t0 = time.perf_counter()
+    sig, ranks = pk.compress(args.kr_eps)
+    t_comp = time.perf_counter() - t0
+    R = pk.info["n"]
+    for _ in range(2):
+        pk.assemble_B(args.form, out=B)
+    torch.cuda.synchronize()
+    lrtei.lrtei_profile_reset()
+    lrtei.lrtei_profile_enable(True)
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    k0.record(stream)
+    for _ in range(reps):
+        pk.assemble_B(args.form, out=B)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    g_ms, g_cnt = lrtei.lrtei_profile_get("tc_gemm")
+    lrtei.lrtei_profile_enable(False)
+    lrtei.lrtei_profile_reset()
+    pk.status()
+    ms = k0.elapsed_time(k1) / reps
+    out = {"eps": args.kr_eps, "ranks_per_dim": [int(r) for r in ranks], "R": R, "n": mol.n,
+           "entries_per_s": whole_job_rate(float(nb2) * nb2, world, ms, device="cuda"), "ms_per_step": ms,
+           "compress_s": t_comp, "tc_gemm_ms_per_step": g_ms / reps, "tc_gemm_launches_per_step": g_cnt / reps,
+           "sigma_R_over_sigma_1": [float(sig[d][min(R, mol.n - 1)] / sig[d][0]) if R < mol.n else 0.0 for d in range(3)]}
+    if Bref is not None:
+        num = den = 0.0
+        for i in range(0, nb2, 4096):
+            num += float(torch.linalg.norm(B[i:i + 4096] - Bref[i:i + 4096])) ** 2
+            den += float(torch.linalg.norm(Bref[i:i + 4096])) ** 2
+        out["rel_err_vs_uncompressed_fp64_B"] = math.sqrt(num / den)
+        del Bref
+    if not args.no_jbuild:
+        Rd = 32
+        D = torch.as_tensor(synth.random_densities(4242, mol.nbf, Rd), device="cuda")
+        J = torch.empty_like(D)
+        for _ in range(2):
+            pk.jbuild(D, out=J)
+        torch.cuda.synchronize()
+        k0.record(stream)
+        for _ in range(3):
+            pk.jbuild(D, out=J)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        jms = k0.elapsed_time(k1) / 3
+        out["jbuilds_per_s"] = world * Rd / (max_over_ranks(jms, world, device="cuda") / 1e3)
+        del D, J
+    pk.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args, world, budget_gb: float = 170.0):

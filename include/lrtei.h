@@ -90,6 +90,8 @@ typedef struct {
   int last_form;    /* lrtei_form used by the last lrtei_assemble_B call */
   size_t workspace_bytes; /* device bytes the plan currently holds */
   double tau_screening;   /* primitive-pair screening threshold of the plan (0: none) */
+  int cheb_n;       /* Chebyshev nodes per dimension the plan was created with */
+  int kr_rank;      /* 0, or the rank R after lrtei_plan_compress (then n == R) */
 } lrtei_plan_info;
 
 /* ---- basis (Section 1, eq. "basis"/"primi") ------------------------------------------
@@ -167,6 +169,22 @@ lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d_idx4, int6
  * (d, row, m), rows ordered by unique pair then j = j1*I_nu + j2; d_c: nrows coefficients c_j. */
 lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d_s, double* d_w, double* d_c,
                            void* stream);
+
+/* ---- Khatri-Rao low-rank compression (Section 6, eq. SVD and eq. approxepsilon) ----------
+ * Computes, on the device in FP64, the SVD of the three moment matrices W~_d = S_d (all
+ * primitive-pair rows x n) by two Jacobi passes on n x n Gram matrices, keeps in dimension d the
+ * R_d leading right singular vectors V_d (R_d = number of singular values >= eps * sigma_1; eps = 0
+ * keeps all n), and replaces the plan's factors by S_d V_d (rows x R) and V_d^T A_d^(p) V_d
+ * (R x R), with R = max_d R_d (capped at max_rank when max_rank > 0).  Every later call of the plan
+ * (B, entries, factors, K, J-builds) then computes eq. approxepsilon,
+ *   B ~ (w/sqrt(pi)) U~ [sum_p w_p (x)_d V_d^T A_d^(p) V_d] U~^T,
+ * whose difference from the uncompressed B is set by the dropped singular values.  The plan's n
+ * becomes R (lrtei_plan_info: n = kr_rank = R, cheb_n = the original n); tables built from the
+ * uncompressed factors are dropped.  A plan is compressed at most once (LRTEI_ERR_UNSUPPORTED).
+ * Host outputs, may be NULL: h_sigma[3 * n] the singular values of each S_d (descending, the
+ * original n), h_ranks[3] the R_d.  Synchronises `stream`.  eps in [0, 1), max_rank in [0, n]. */
+lrtei_status lrtei_plan_compress(lrtei_plan* plan, double eps, int max_rank, double* h_sigma, int* h_ranks,
+                                 void* stream);
 
 /* ---- node sum of the factored form (Theorem 1, factored form; eq. approx33) ---------------
  * d_K: n^3 x n^3 FP64, row-major, K((a1 n + a2) n + a3, (b1 n + b2) n + b3) =

@@ -48,6 +48,17 @@ def truncated_factors(S: np.ndarray, rank: int):
     return u[:, :rank] * sv[:rank], vt[:rank].T, sv
 
 
+def ranks_for_eps(o, eps: float):
+    """eq. approxepsilon's truncation, read as: keep in dimension d the singular values of W~^(d)
+    that are at least eps times the largest (eps = 0 keeps all n)."""
+    S, _, _ = moment_rows(o)
+    out = []
+    for d in range(3):
+        sv = np.linalg.svd(S[d], compute_uv=False)
+        out.append(o.n if eps == 0 else max(1, int(np.count_nonzero(sv >= eps * sv[0]))))
+    return out
+
+
 def compressed_Bu(o, ranks: Sequence[int]):
     """B_u (unique pairs x unique pairs) by eq. approxepsilon with ranks (R_1, R_2, R_3); also
     returns the three singular value vectors."""

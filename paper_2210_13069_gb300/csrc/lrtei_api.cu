@@ -58,6 +58,9 @@ struct lrtei_plan {
   lrtei_precision prec = LRTEI_FP64;
   double tau = 0.0;  // primitive-pair screening threshold
   int last_form = 0;
+  int cheb_n = 0;         // Chebyshev nodes per dimension (n before a Khatri-Rao compression)
+  int kr_rank = 0;        // 0, or the common rank R of the compressed moment matrices (n == R then)
+  int kr_ranks[3] = {0, 0, 0};
   PairTable t;
   // device data
   int *d_bf_shell = nullptr, *d_bf_pow = nullptr, *d_shell_nprim = nullptr, *d_shell_poff = nullptr,
@@ -213,6 +216,7 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   pl->P = P;
   pl->prec = precision;
   pl->tau = tau_screening;
+  pl->cheb_n = n;
   const lrtei_basis& b = pl->basis;
   // box (eq. compact)
   if (box_lo) {
@@ -420,6 +424,8 @@ lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info) 
   info->last_form = plan->last_form;
   info->workspace_bytes = plan->bytes;
   info->tau_screening = plan->tau;
+  info->cheb_n = plan->cheb_n;
+  info->kr_rank = plan->kr_rank;
   return LRTEI_OK;
 }
 
@@ -1088,6 +1094,87 @@ lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream) {
                               (cudaStream_t)stream));
   }
   return finish_launch("dense K");
+}
+
+// Khatri-Rao low-rank compression (Section 6, eq. SVD and eq. approxepsilon): S_d -> S_d V_d and
+// A_d^(p) -> V_d^T A_d^(p) V_d with V_d the leading right singular vectors of S_d; every later call
+// runs on the compressed factors (the plan's n becomes the rank R).
+lrtei_status lrtei_plan_compress(lrtei_plan* plan, double eps, int max_rank, double* h_sigma, int* h_ranks,
+                                 void* stream) {
+  if (!plan) { set_error("plan is NULL"); return LRTEI_ERR_ARG; }
+  if (!(eps >= 0.0 && eps < 1.0)) { set_error("eps must be in [0, 1) (got %g)", eps); return LRTEI_ERR_ARG; }
+  if (max_rank < 0 || max_rank > plan->n) {
+    set_error("max_rank must be in [0, n = %d] (got %d)", plan->n, max_rank);
+    return LRTEI_ERR_ARG;
+  }
+  if (plan->kr_rank > 0) { set_error("the plan is already compressed (rank %d)", plan->kr_rank); return LRTEI_ERR_UNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = plan->n, P = plan->P;
+  const int64_t nrows = plan->t.nrows;
+  if (nrows == 0) { set_error("the plan has no primitive-pair rows"); return LRTEI_ERR_ARG; }
+  std::vector<double> lam(3 * (size_t)n);
+  double *part, *G, *V1, *V, *dlam;
+  {
+    Scratch sc(st);
+    LRTEI_TRY(sc.get(&part, (size_t)kr_gram_blocks(nrows) * 3 * n * n));
+    LRTEI_TRY(sc.get(&G, 3 * (size_t)n * n));
+    LRTEI_TRY(sc.get(&V1, 3 * (size_t)n * n));
+    LRTEI_TRY(sc.get(&dlam, 3 * (size_t)n));
+    double* Vk;
+    LRTEI_TRY(plan->alloc(&Vk, 3 * (size_t)n * n));  // kept until the projection below has run
+    V = Vk;
+    {
+      ProfScope ps("kr_svd", st);
+      LRTEI_CUDA(launch_kr_svd(nrows, n, plan->d_S, part, G, V1, dlam, V, nullptr, st));
+    }
+    LRTEI_CUDA(cudaMemcpyAsync(lam.data(), dlam, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    LRTEI_CUDA(cudaStreamSynchronize(st));
+  }
+  int R = 0, Rd[3];
+  for (int d = 0; d < 3; ++d) {
+    const double s0 = sqrt(std::max(lam[(size_t)d * n], 0.0));
+    int r = n;
+    if (eps > 0.0) {
+      r = 0;
+      while (r < n && sqrt(std::max(lam[(size_t)d * n + r], 0.0)) >= eps * s0 && s0 > 0.0) ++r;
+      r = std::max(r, 1);
+    }
+    Rd[d] = r;
+    R = std::max(R, r);
+    if (h_sigma)
+      for (int i = 0; i < n; ++i) h_sigma[(size_t)d * n + i] = sqrt(std::max(lam[(size_t)d * n + i], 0.0));
+  }
+  if (max_rank > 0) R = std::min(R, max_rank);
+  if (h_ranks) for (int d = 0; d < 3; ++d) h_ranks[d] = Rd[d];
+  double *Snew, *Cnew;
+  LRTEI_TRY(plan->alloc(&Snew, 3 * (size_t)nrows * R));
+  LRTEI_TRY(plan->alloc(&Cnew, 3 * (size_t)P * R * R));
+  {
+    ProfScope ps("kr_project", st);
+    LRTEI_CUDA(launch_kr_project(nrows, n, P, R, plan->d_S, plan->d_C, V, Snew, Cnew, st));
+  }
+  LRTEI_CUDA(cudaStreamSynchronize(st));
+  // the tables built from the uncompressed factors are stale now
+  forget_plan_graphs(plan);
+  const int64_t n3 = (int64_t)n * n * n;
+  plan->release(plan->d_T, sizeof(double) * 3 * (size_t)P * nrows * n);
+  plan->d_T = nullptr;
+  plan->release(plan->d_F, sizeof(double) * (size_t)plan->t.npair * n3);
+  plan->d_F = nullptr;
+  plan->release(plan->d_F32, sizeof(float) * (size_t)plan->t.npair * n3);
+  plan->d_F32 = nullptr;
+  if (plan->have_Fsp) { release_split(plan, plan->Fsp); plan->have_Fsp = false; }
+  if (plan->have_Ksp) { release_split(plan, plan->Ksp); plan->have_Ksp = false; }
+  if (plan->have_FTsp) { release_split(plan, plan->FTsp); plan->have_FTsp = false; }
+  plan->release(plan->d_S, sizeof(double) * 3 * (size_t)nrows * n);
+  plan->release(plan->d_C, sizeof(double) * 3 * (size_t)P * n * n);
+  plan->release(V, sizeof(double) * 3 * (size_t)n * n);
+  plan->d_S = Snew;
+  plan->d_C = Cnew;
+  plan->n = R;
+  plan->kr_rank = R;
+  for (int d = 0; d < 3; ++d) plan->kr_ranks[d] = Rd[d];
+  return finish_launch("Khatri-Rao compression");
 }
 
 static lrtei_status jbuild_tc(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st) {

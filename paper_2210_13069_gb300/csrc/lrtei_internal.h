@@ -159,6 +159,18 @@ void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStr
 // Unique-pair results -> full symmetric J: J_q(mu,nu) = J_q(nu,mu) = scale * Ju[r][q].
 void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, int* d_status, cudaStream_t st);
 
+// ---------------------------------------------------------------- Khatri-Rao compression
+// Scratch blocks of the Gram partial sums (d_part holds kr_gram_blocks * 3 * n * n doubles).
+int kr_gram_blocks(int64_t nrows);
+// Right singular vectors d_V (3 x n x n, columns descending) and squared singular values d_lam
+// (3 x n, descending) of the three moment matrices S_d (nrows x n), by two Jacobi passes on Gram
+// matrices; d_G, d_V1: 3 n n scratch; d_sweeps (6 ints, may be NULL): sweeps of each solve.
+cudaError_t launch_kr_svd(int64_t nrows, int n, const double* d_S, double* d_part, double* d_G, double* d_V1,
+                          double* d_lam, double* d_V, int* d_sweeps, cudaStream_t st);
+// S_new = S_d V_d[:, :R] (3 x nrows x R) and C_new = V_d^T A_d^(p) V_d (3 x P x R x R).
+cudaError_t launch_kr_project(int64_t nrows, int n, int P, int R, const double* d_S, const double* d_C,
+                              const double* d_V, double* d_Snew, double* d_Cnew, cudaStream_t st);
+
 // ---------------------------------------------------------------- CUDA-core GEMM
 // C[M x N] = alpha * op(A) op(B) + beta * C, row-major; transA: A is K x M; transB: B is N x K.
 template <typename T>

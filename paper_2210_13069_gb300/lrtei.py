@@ -37,7 +37,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("nbf", ctypes.c_int), ("npair", ctypes.c_int64), ("nrows", ctypes.c_int64), ("n", ctypes.c_int),
                 ("P", ctypes.c_int), ("omega", ctypes.c_double), ("box_lo", ctypes.c_double * 3),
                 ("box_hi", ctypes.c_double * 3), ("precision", ctypes.c_int), ("last_form", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_size_t), ("tau_screening", ctypes.c_double)]
+                ("workspace_bytes", ctypes.c_size_t), ("tau_screening", ctypes.c_double), ("cheb_n", ctypes.c_int),
+                ("kr_rank", ctypes.c_int)]
 
 
 _lib = None
@@ -76,6 +77,7 @@ def load():
         "lrtei_entries_noalloc": (S, [VP, VP, ctypes.c_int64, VP, VP]),
         "lrtei_factors": (S, [VP, VP, VP, VP, VP, VP, VP]),
         "lrtei_dense_K": (S, [VP, VP, VP]),
+        "lrtei_plan_compress": (S, [VP, ctypes.c_double, ctypes.c_int, DP, IP, VP]),
         "lrtei_jbuild": (S, [VP, VP, ctypes.c_int, VP, VP]),
         "lrtei_jbuild_batched": (S, [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(VP), IP, ctypes.POINTER(VP),
                                      VP]),
@@ -188,7 +190,7 @@ def lrtei_plan_info_get(plan: int) -> dict:
     return {"nbf": info.nbf, "npair": info.npair, "nrows": info.nrows, "n": info.n, "P": info.P,
             "omega": info.omega, "box_lo": list(info.box_lo), "box_hi": list(info.box_hi),
             "precision": info.precision, "last_form": info.last_form, "workspace_bytes": info.workspace_bytes,
-            "tau_screening": info.tau_screening}
+            "tau_screening": info.tau_screening, "cheb_n": info.cheb_n, "kr_rank": info.kr_rank}
 
 
 def lrtei_plan_status(plan: int):
@@ -216,6 +218,16 @@ def lrtei_entries_noalloc(plan: int, d_idx4, count: int, d_out, stream=None):
 
 def lrtei_factors(plan: int, d_S=None, d_C=None, d_s=None, d_w=None, d_c=None, stream=None):
     _check(load().lrtei_factors(plan, _ptr(d_S), _ptr(d_C), _ptr(d_s), _ptr(d_w), _ptr(d_c), _stream(stream)))
+
+
+def lrtei_plan_compress(plan: int, eps: float, max_rank: int = 0, n: Optional[int] = None, stream=None):
+    """Khatri-Rao compression of the plan's factors; returns (singular values 3 x n, ranks R_d)."""
+    n = n if n is not None else lrtei_plan_info_get(plan)["n"]
+    sig = np.zeros(3 * n, dtype=np.float64)
+    ranks = np.zeros(3, dtype=np.int32)
+    _check(load().lrtei_plan_compress(plan, float(eps), int(max_rank), sig.ctypes.data_as(DP),
+                                      ranks.ctypes.data_as(IP), _stream(stream)))
+    return sig.reshape(3, n), ranks
 
 
 def lrtei_dense_K(plan: int, d_K, stream=None):
@@ -397,6 +409,12 @@ class Plan:
             out = torch.empty_like(D)
         lrtei_jbuild(self.plan, D, D.shape[0], out, stream)
         return out
+
+    def compress(self, eps: float, max_rank: int = 0, stream=None):
+        """Khatri-Rao compression (eq. approxepsilon); returns (singular values, ranks R_d)."""
+        sig, ranks = lrtei_plan_compress(self.plan, eps, max_rank, self.info["n"], stream)
+        self.info = lrtei_plan_info_get(self.plan)
+        return sig, ranks
 
     def status(self):
         lrtei_plan_status(self.plan)
