@@ -164,6 +164,17 @@ lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t coun
 lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d_idx4, int64_t count, double* d_out,
                                    void* stream);
 
+/* ---- entries at other orders (error sweeps of the plain method) ---------------------------
+ * Algorithm 1 entries of the plan's basis, box and omega at ncombo other orders (n_c, P_c) =
+ * (h_n[c], h_P[c]), 1 <= n_c <= the plan's n, 1 <= P_c <= 128 (host arrays): the moment integrals
+ * of eq. defV do not depend on n, so the plan's moments serve every n_c <= n through their first
+ * n_c columns; the Gauss-Legendre nodes (eq. TEI2) and Chebyshev coefficients (Definition 1) are
+ * computed for each order.  d_idx4 as for lrtei_entries; d_out: device double[ncombo * count],
+ * order-major (d_out[c * count + e]).  These sweeps are the selector's training data.  Plans
+ * compressed by lrtei_plan_compress return LRTEI_ERR_UNSUPPORTED. */
+lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const int* h_n, const int* h_P, const int32_t* d_idx4,
+                                  int64_t count, double* d_out, void* stream);
+
 /* ---- factors (Theorem 1: w_p, s_p, A^(p), W~ = S_d) ---------------------------------------
  * Any pointer may be NULL.  d_s, d_w: P doubles; d_C: 3*P*n*n (d, p, a, b); d_S: 3*nrows*n
  * (d, row, m), rows ordered by unique pair then j = j1*I_nu + j2; d_c: nrows coefficients c_j. */
@@ -219,9 +230,13 @@ lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const doub
                                   double* const* d_J, void* stream);
 
 /* ---- the (n, P) selector (a 3-layer MLP, FP32, trained on the GPU) ----------------------
- * Features (6): omega, box half-width, log10 alpha_min, log10 alpha_max, max l, log10 target.
- * Outputs (2): n, P (rounded, clamped to [8, 64] x [8, 96]).  Training data are error sweeps
- * of the plain method (see the Python layer).  Weights live on the device. */
+ * The paper picks the number of Chebyshev nodes with chebfun2 and studies how the error trades
+ * n against P (Section 3.1, Section 6.1); here a network (6 -> H -> H -> 2, ReLU) predicts the
+ * cheapest (n, P) that reaches a requested relative error, trained on error sweeps of the plain
+ * method.  Raw features (6, host doubles): omega, box half-width (bohr), alpha_min, alpha_max,
+ * max angular momentum l, target relative error.  Normalised features: omega, half / 30,
+ * log10 alpha_min, log10 alpha_max / 4, l / 2, -log10 target / 10; normalised outputs:
+ * (n - 8) / 56, (P - 8) / 120.  Weights live on the device. */
 typedef struct lrtei_selector lrtei_selector;
 lrtei_status lrtei_selector_create(int hidden, uint64_t seed, lrtei_selector** out);
 void lrtei_selector_destroy(lrtei_selector* sel);
@@ -239,6 +254,29 @@ int64_t lrtei_selector_nparams(const lrtei_selector* sel);
 /* Parameters to / from host memory (packed as above), for checkpointing. */
 lrtei_status lrtei_selector_get_params(const lrtei_selector* sel, float* h_params);
 lrtei_status lrtei_selector_set_params(lrtei_selector* sel, const float* h_params);
+/* Normalised features of raw[6] into out[6] (host); LRTEI_ERR_ARG unless omega, the half-width,
+ * both exponents and the target are positive and finite and l >= 0. */
+lrtei_status lrtei_selector_features(const double* raw, float* out);
+/* Normalised training target of (n, P) into out[2] (host). */
+lrtei_status lrtei_selector_encode(int n, int P, float* out);
+/* The selection (host in, host out; runs the network on the device and synchronises): if raw
+ * lies inside the training ranges (omega in [0.2, 1], half-width in [3, 34] bohr, log10 alpha_min
+ * in [-1.4, 0.1], log10 alpha_max in [-0.4, 3.4], l in [0, 2], log10 target in [-9, -3]) the
+ * network's (n, P) plus a margin of (4, 8), each rounded up to the grids
+ * n in {8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64}, P in {8, 12, ..., 96, 128}; otherwise the
+ * conservative fixed (32, 48).  *used_fallback (may be NULL) tells which. */
+lrtei_status lrtei_select_np(lrtei_selector* sel, const double* raw, int* n, int* P, int* used_fallback);
+/* Training: `epochs` epochs of lrtei_selector_train_epoch on (d_X, d_Y), at rate lr for the first
+ * two thirds and lr / 10 after; h_loss[epochs] (may be NULL) receives each epoch's mean loss. */
+lrtei_status lrtei_selector_train(lrtei_selector* sel, const float* d_X, const float* d_Y, int N, int epochs,
+                                  int batch, float lr, float* h_loss, void* stream);
+/* Checkpoints: a versioned little-endian file ("LRTEISEL", version 2, hidden width, parameter
+ * count, an optional caller text `meta`, the FP32 parameters, an FNV-1a 64-bit checksum of all
+ * preceding bytes).  Load rejects another version, inconsistent sizes or a checksum mismatch
+ * (LRTEI_ERR_ARG) and creates a selector with those parameters (Adam state zero); meta (may be
+ * NULL) receives the text, truncated to meta_cap - 1 bytes. */
+lrtei_status lrtei_selector_save(const lrtei_selector* sel, const char* path, const char* meta);
+lrtei_status lrtei_selector_load(const char* path, lrtei_selector** out, char* meta, size_t meta_cap);
 
 /* ---- kernel timing (tracing) ----------------------------------------------------------
  * When enabled, the library records a pair of CUDA events on the launching stream around each

@@ -6,6 +6,7 @@
 // memory; gradients are reduced per block in shared memory and added to the global gradient
 // with one atomic per parameter per block.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -149,6 +150,7 @@ struct lrtei_selector {
   float* d_v = nullptr;
   float* d_grad = nullptr;
   float* d_loss = nullptr;
+  float* d_io = nullptr;  // one feature row and its two outputs (lrtei_select_np)
   int* d_idx = nullptr;
   int idx_cap = 0;
   int64_t step = 0;
@@ -223,6 +225,7 @@ void lrtei_selector_destroy(lrtei_selector* s) {
   cudaFree(s->d_v);
   cudaFree(s->d_grad);
   cudaFree(s->d_loss);
+  cudaFree(s->d_io);
   cudaFree(s->d_idx);
   delete s;
 }
@@ -314,6 +317,205 @@ lrtei_status lrtei_selector_set_params(lrtei_selector* s, const float* h_params)
   using namespace lrtei;
   if (!s || !h_params) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
   LRTEI_CUDA(cudaMemcpy(s->d_params, h_params, sizeof(float) * s->np, cudaMemcpyHostToDevice));
+  return LRTEI_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ selection policy
+// The network maps normalised features of an instance to the normalised cheapest (n, P) that met
+// a target in the error sweeps; the policy around it (feature normalisation, training ranges,
+// fallback, margins and the grids) lives here so that a caller selects (n, P) through the C ABI
+// alone.
+namespace lrtei {
+namespace selpol {
+constexpr int kNGrid[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64};      // last: N_MAX
+constexpr int kPGrid[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 80, 96, 128};  // last: P_MAX
+constexpr int kFallbackN = 32, kFallbackP = 48, kMarginN = 4, kMarginP = 8;
+// training ranges of (omega, box half-width, log10 alpha_min, log10 alpha_max, max l, log10 target)
+constexpr double kLo[6] = {0.2, 3.0, -1.4, -0.4, 0.0, -9.0};
+constexpr double kHi[6] = {1.0, 34.0, 0.1, 3.4, 2.0, -3.0};
+
+bool valid_raw(const double* raw) {
+  for (int i = 0; i < 6; ++i)
+    if (!isfinite(raw[i])) return false;
+  return raw[0] > 0.0 && raw[1] > 0.0 && raw[2] > 0.0 && raw[3] > 0.0 && raw[4] >= 0.0 && raw[5] > 0.0;
+}
+void features(const double* raw, float* out) {
+  out[0] = (float)raw[0];
+  out[1] = (float)(raw[1] / 30.0);
+  out[2] = (float)log10(raw[2]);
+  out[3] = (float)(log10(raw[3]) / 4.0);
+  out[4] = (float)(raw[4] / 2.0);
+  out[5] = (float)(-log10(raw[5]) / 10.0);
+}
+bool in_range(const double* raw) {
+  const double v[6] = {raw[0], raw[1], log10(raw[2]), log10(raw[3]), raw[4], log10(raw[5])};
+  for (int i = 0; i < 6; ++i)
+    if (v[i] < kLo[i] - 1e-9 || v[i] > kHi[i] + 1e-9) return false;
+  return true;
+}
+template <size_t K>
+int round_up(const int (&grid)[K], double x) {
+  for (size_t i = 0; i < K; ++i)
+    if (grid[i] >= x) return grid[i];
+  return grid[K - 1];
+}
+
+// FNV-1a, 64 bit, over the checkpoint's bytes.
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ULL) {
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+constexpr char kMagic[8] = {'L', 'R', 'T', 'E', 'I', 'S', 'E', 'L'};
+constexpr uint32_t kVersion = 2;
+}  // namespace selpol
+}  // namespace lrtei
+
+extern "C" {
+
+lrtei_status lrtei_selector_features(const double* raw, float* out) {
+  using namespace lrtei;
+  if (!raw || !out) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (!selpol::valid_raw(raw)) {
+    set_error("selector features: omega, box half-width, exponents and target must be positive and finite");
+    return LRTEI_ERR_ARG;
+  }
+  selpol::features(raw, out);
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_selector_encode(int n, int P, float* out) {
+  using namespace lrtei;
+  if (!out || n < 1 || P < 1) { set_error("invalid selector encode arguments"); return LRTEI_ERR_ARG; }
+  out[0] = (float)((n - 8.0) / 56.0);
+  out[1] = (float)((P - 8.0) / 120.0);
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_select_np(lrtei_selector* sel, const double* raw, int* n, int* P, int* used_fallback) {
+  using namespace lrtei;
+  if (!sel || !raw || !n || !P) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (!selpol::valid_raw(raw)) {
+    set_error("select_np: omega, box half-width, exponents and target must be positive and finite");
+    return LRTEI_ERR_ARG;
+  }
+  if (!selpol::in_range(raw)) {  // outside the trained ranges: the conservative fixed orders
+    *n = selpol::kFallbackN;
+    *P = selpol::kFallbackP;
+    if (used_fallback) *used_fallback = 1;
+    return LRTEI_OK;
+  }
+  float h[8];
+  selpol::features(raw, h);
+  if (!sel->d_io) {
+    count_alloc();
+    LRTEI_CUDA(cudaMalloc(&sel->d_io, sizeof(float) * 8));
+  }
+  LRTEI_CUDA(cudaMemcpy(sel->d_io, h, sizeof(float) * mlp::kIn, cudaMemcpyHostToDevice));
+  count_launch();
+  mlp::k_forward<<<1, mlp::kThreads, smem_fwd(sel->hidden)>>>(sel->d_params, sel->hidden, sel->d_io, 1,
+                                                              sel->d_io + mlp::kIn);
+  LRTEI_CUDA(cudaGetLastError());
+  LRTEI_CUDA(cudaMemcpy(h + mlp::kIn, sel->d_io + mlp::kIn, sizeof(float) * mlp::kOut, cudaMemcpyDeviceToHost));
+  const double nf = 8.0 + 56.0 * h[mlp::kIn], pf = 8.0 + 120.0 * h[mlp::kIn + 1];
+  if (!isfinite(nf) || !isfinite(pf)) { set_error("selector network output is not finite"); return LRTEI_ERR_NUMERIC; }
+  *n = selpol::round_up(selpol::kNGrid, nf + selpol::kMarginN);
+  *P = selpol::round_up(selpol::kPGrid, pf + selpol::kMarginP);
+  if (used_fallback) *used_fallback = 0;
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_selector_train(lrtei_selector* sel, const float* d_X, const float* d_Y, int N, int epochs,
+                                  int batch, float lr, float* h_loss, void* stream) {
+  using namespace lrtei;
+  if (!sel || epochs <= 0) { set_error("invalid selector train arguments"); return LRTEI_ERR_ARG; }
+  for (int ep = 0; ep < epochs; ++ep) {
+    const float cur = ep < epochs * 2 / 3 ? lr : 0.1f * lr;  // step decay for the last third
+    float l = 0.f;
+    const lrtei_status s = lrtei_selector_train_epoch(sel, d_X, d_Y, N, batch, cur, h_loss ? &l : nullptr, stream);
+    if (s != LRTEI_OK) return s;
+    if (h_loss) h_loss[ep] = l;
+  }
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_selector_save(const lrtei_selector* sel, const char* path, const char* meta) {
+  using namespace lrtei;
+  if (!sel || !path) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  std::vector<float> params((size_t)sel->np);
+  LRTEI_CUDA(cudaMemcpy(params.data(), sel->d_params, sizeof(float) * sel->np, cudaMemcpyDeviceToHost));
+  const uint32_t mlen = meta ? (uint32_t)strlen(meta) : 0u;
+  std::vector<unsigned char> buf;
+  auto put = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    buf.insert(buf.end(), c, c + n);
+  };
+  const uint32_t ver = selpol::kVersion, hid = (uint32_t)sel->hidden;
+  const uint64_t np = (uint64_t)sel->np;
+  put(selpol::kMagic, 8);
+  put(&ver, 4);
+  put(&hid, 4);
+  put(&np, 8);
+  put(&mlen, 4);
+  if (mlen) put(meta, mlen);
+  put(params.data(), sizeof(float) * params.size());
+  const uint64_t sum = selpol::fnv1a(buf.data(), buf.size());
+  put(&sum, 8);
+  FILE* f = fopen(path, "wb");
+  if (!f) { set_error("cannot open %s for writing", path); return LRTEI_ERR_ARG; }
+  const size_t w = fwrite(buf.data(), 1, buf.size(), f);
+  const int c = fclose(f);
+  if (w != buf.size() || c != 0) { set_error("writing %s failed", path); return LRTEI_ERR_ARG; }
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_selector_load(const char* path, lrtei_selector** out, char* meta, size_t meta_cap) {
+  using namespace lrtei;
+  if (!path || !out) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) { set_error("cannot open %s", path); return LRTEI_ERR_ARG; }
+  std::vector<unsigned char> buf;
+  unsigned char tmp[65536];
+  size_t r;
+  while ((r = fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
+  fclose(f);
+  const size_t head = 8 + 4 + 4 + 8 + 4;
+  if (buf.size() < head + 8 || memcmp(buf.data(), selpol::kMagic, 8) != 0) {
+    set_error("%s is not a selector checkpoint", path);
+    return LRTEI_ERR_ARG;
+  }
+  uint32_t ver, hid, mlen;
+  uint64_t np, sum;
+  memcpy(&ver, buf.data() + 8, 4);
+  memcpy(&hid, buf.data() + 12, 4);
+  memcpy(&np, buf.data() + 16, 8);
+  memcpy(&mlen, buf.data() + 24, 4);
+  if (ver != selpol::kVersion) { set_error("selector checkpoint version %u, this library reads %u", ver, selpol::kVersion); return LRTEI_ERR_ARG; }
+  if (hid < 1 || hid > (uint32_t)mlp::kMaxH || np != (uint64_t)mlp::nparams((int)hid) ||
+      buf.size() != head + mlen + np * sizeof(float) + 8) {
+    set_error("selector checkpoint %s: inconsistent sizes", path);
+    return LRTEI_ERR_ARG;
+  }
+  memcpy(&sum, buf.data() + buf.size() - 8, 8);
+  if (selpol::fnv1a(buf.data(), buf.size() - 8) != sum) { set_error("selector checkpoint %s: checksum mismatch", path); return LRTEI_ERR_ARG; }
+  if (meta && meta_cap > 0) {
+    const size_t k = std::min((size_t)mlen, meta_cap - 1);
+    memcpy(meta, buf.data() + head, k);
+    meta[k] = 0;
+  }
+  lrtei_selector* s = nullptr;
+  lrtei_status st = lrtei_selector_create((int)hid, 0, &s);
+  if (st != LRTEI_OK) return st;
+  std::vector<float> params((size_t)np);
+  memcpy(params.data(), buf.data() + head + mlen, sizeof(float) * np);
+  st = lrtei_selector_set_params(s, params.data());
+  if (st != LRTEI_OK) { lrtei_selector_destroy(s); return st; }
+  *out = s;
   return LRTEI_OK;
 }
 

@@ -1431,6 +1431,8 @@ lrtei_status plan_view(const lrtei_plan* plan, PlanView* v) {
   v->C = plan->d_C;
   v->w = plan->d_w;
   v->status = plan->d_status;
+  v->half3 = plan->d_half3;
+  v->kr_rank = plan->kr_rank;
   return LRTEI_OK;
 }
 }  // namespace lrtei

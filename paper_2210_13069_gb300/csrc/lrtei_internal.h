@@ -225,6 +225,8 @@ struct PlanView {
   const double* C;  // 3 x P x n x n Chebyshev coefficients
   const double* w;  // P quadrature weights
   int* status;      // the plan's device status word
+  const double* half3;  // box half-widths per dimension (device)
+  int kr_rank;      // 0, or the rank of a Khatri-Rao compressed plan
 };
 lrtei_status plan_view(const lrtei_plan* plan, PlanView* v);
 

@@ -75,6 +75,7 @@ def load():
         "lrtei_assemble_Bu_rows": (S, [VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, VP, ctypes.c_int64, VP]),
         "lrtei_entries": (S, [VP, VP, ctypes.c_int64, VP, VP]),
         "lrtei_entries_noalloc": (S, [VP, VP, ctypes.c_int64, VP, VP]),
+        "lrtei_entries_orders": (S, [VP, ctypes.c_int, IP, IP, VP, ctypes.c_int64, VP, VP]),
         "lrtei_factors": (S, [VP, VP, VP, VP, VP, VP, VP]),
         "lrtei_dense_K": (S, [VP, VP, VP]),
         "lrtei_plan_compress": (S, [VP, ctypes.c_double, ctypes.c_int, DP, IP, VP]),
@@ -90,6 +91,13 @@ def load():
         "lrtei_selector_nparams": (ctypes.c_int64, [VP]),
         "lrtei_selector_get_params": (S, [VP, ctypes.POINTER(ctypes.c_float)]),
         "lrtei_selector_set_params": (S, [VP, ctypes.POINTER(ctypes.c_float)]),
+        "lrtei_selector_features": (S, [DP, ctypes.POINTER(ctypes.c_float)]),
+        "lrtei_selector_encode": (S, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+        "lrtei_select_np": (S, [VP, DP, IP, IP, IP]),
+        "lrtei_selector_train": (S, [VP, VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                     ctypes.POINTER(ctypes.c_float), VP]),
+        "lrtei_selector_save": (S, [VP, ctypes.c_char_p, ctypes.c_char_p]),
+        "lrtei_selector_load": (S, [ctypes.c_char_p, ctypes.POINTER(VP), ctypes.c_char_p, ctypes.c_size_t]),
         "lrtei_profile_enable": (S, [ctypes.c_int]),
         "lrtei_profile_get": (S, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "lrtei_profile_reset": (None, []),
@@ -216,6 +224,15 @@ def lrtei_entries_noalloc(plan: int, d_idx4, count: int, d_out, stream=None):
     _check(load().lrtei_entries_noalloc(plan, _ptr(d_idx4), int(count), _ptr(d_out), _stream(stream)))
 
 
+def lrtei_entries_orders(plan: int, ns, Ps, d_idx4, count: int, d_out, stream=None):
+    n = _np(ns, np.int32)
+    P = _np(Ps, np.int32)
+    if n.size != P.size:
+        raise LrteiError(1, "ns and Ps differ in length")
+    _check(load().lrtei_entries_orders(plan, int(n.size), n.ctypes.data_as(IP), P.ctypes.data_as(IP), _ptr(d_idx4),
+                                       int(count), _ptr(d_out), _stream(stream)))
+
+
 def lrtei_factors(plan: int, d_S=None, d_C=None, d_s=None, d_w=None, d_c=None, stream=None):
     _check(load().lrtei_factors(plan, _ptr(d_S), _ptr(d_C), _ptr(d_s), _ptr(d_w), _ptr(d_c), _stream(stream)))
 
@@ -318,6 +335,46 @@ def lrtei_selector_set_params(sel: int, params: np.ndarray):
     if p.size != lrtei_selector_nparams(sel):
         raise LrteiError(1, "parameter count mismatch")
     _check(load().lrtei_selector_set_params(sel, p.ctypes.data_as(FP)))
+
+
+def lrtei_selector_features(raw) -> np.ndarray:
+    r = _np(raw, np.float64).reshape(6)
+    out = np.zeros(6, dtype=np.float32)
+    _check(load().lrtei_selector_features(r.ctypes.data_as(DP), out.ctypes.data_as(FP)))
+    return out
+
+
+def lrtei_selector_encode(n: int, P: int) -> np.ndarray:
+    out = np.zeros(2, dtype=np.float32)
+    _check(load().lrtei_selector_encode(int(n), int(P), out.ctypes.data_as(FP)))
+    return out
+
+
+def lrtei_select_np(sel: int, raw):
+    """(n, P, used_fallback) for raw features (omega, half-width, alpha_min, alpha_max, l, target)."""
+    r = _np(raw, np.float64).reshape(6)
+    n, P, fb = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().lrtei_select_np(sel, r.ctypes.data_as(DP), ctypes.byref(n), ctypes.byref(P), ctypes.byref(fb)))
+    return n.value, P.value, bool(fb.value)
+
+
+def lrtei_selector_train(sel: int, d_X, d_Y, N: int, epochs: int, batch: int, lr: float, stream=None) -> np.ndarray:
+    hist = np.zeros(int(epochs), dtype=np.float32)
+    _check(load().lrtei_selector_train(sel, _ptr(d_X), _ptr(d_Y), int(N), int(epochs), int(batch), float(lr),
+                                       hist.ctypes.data_as(FP), _stream(stream)))
+    return hist
+
+
+def lrtei_selector_save(sel: int, path: str, meta: str = ""):
+    _check(load().lrtei_selector_save(sel, path.encode(), meta.encode() if meta else None))
+
+
+def lrtei_selector_load(path: str, meta_cap: int = 1 << 16):
+    """(selector handle, meta text)."""
+    out = VP()
+    buf = ctypes.create_string_buffer(meta_cap)
+    _check(load().lrtei_selector_load(path.encode(), ctypes.byref(out), buf, meta_cap))
+    return out.value, buf.value.decode()
 
 
 def lrtei_last_error() -> str:

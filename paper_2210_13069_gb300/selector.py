@@ -1,24 +1,22 @@
-"""Learned choice of the Chebyshev order n and the quadrature size P.
+"""Learned choice of the Chebyshev order n and the quadrature size P: sweep orchestration and
+marshalling around the library's selector calls.
 
 The paper picks the number of interpolation nodes per quadrature node with chebfun2 and shows
 how the error trades n against P (Section 3.1, Section 6.1).  Here a small MLP (6 -> 64 -> 64
 -> 2, trained on the GPU by the library's own forward/backward/Adam kernels) maps
-    (omega, box half-width, log10 alpha_min, log10 alpha_max, max l, log10 target)
-to the cheapest (n, P) that reached the target error in error sweeps of the plain method:
-entries of B computed by the library at each (n, P) against the same entries at a high
-reference order.  Out of the trained range, or if asked, the conservative fixed (32, 48) is
-used instead.
+    (omega, box half-width, alpha_min, alpha_max, max l, target)
+to the cheapest (n, P) that reached the target error in error sweeps of the plain method.
+Feature normalisation, the training ranges, the fallback to the conservative fixed (32, 48),
+the margins and the rounding to the grids, training and checkpoints all live in the library
+(lrtei_selector_features / _encode / lrtei_select_np / lrtei_selector_train / _save / _load);
+this module draws the sweep instances, runs the sweeps through lrtei_entries_orders and builds
+the labels.
 
-Every number here comes from the CUDA library (Algorithm 1 entries); nothing calls the CPU
-oracle.
+Every number here comes from the CUDA library; nothing calls the CPU oracle.
 """
 from __future__ import annotations
 
-import hashlib
-import io
 import json
-import math
-from dataclasses import dataclass
 from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -30,34 +28,18 @@ P_GRID = [8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 80, 96]
 N_REF, P_REF = 64, 128
 TARGETS = [10.0 ** -k for k in range(3, 10)]
 FALLBACK = (32, 48)
-N_MAX, P_MAX = 64, 128
-# training ranges of the features (inference outside them falls back)
-RANGES = {"omega": (0.2, 1.0), "half": (3.0, 34.0), "lamin": (-1.4, 0.1), "lamax": (-0.4, 3.4), "lmax": (0, 2),
-          "ltarget": (-9.0, -3.0)}
 
 
 def features(omega: float, half: float, amin: float, amax: float, lmax: int, target: float) -> np.ndarray:
-    """Normalised feature vector of one instance."""
-    return np.array([omega, half / 30.0, math.log10(amin), math.log10(amax) / 4.0, lmax / 2.0,
-                     -math.log10(target) / 10.0], dtype=np.float32)
-
-
-def in_range(omega, half, amin, amax, lmax, target) -> bool:
-    r = RANGES
-    vals = {"omega": omega, "half": half, "lamin": math.log10(amin), "lamax": math.log10(amax), "lmax": lmax,
-            "ltarget": math.log10(target)}
-    return all(r[k][0] - 1e-9 <= v <= r[k][1] + 1e-9 for k, v in vals.items())
+    """Normalised feature vector of one instance (computed by the library)."""
+    return lrtei.lrtei_selector_features([omega, half, amin, amax, lmax, target])
 
 
 def encode_targets(n: float, P: float) -> np.ndarray:
-    return np.array([(n - 8.0) / 56.0, (P - 8.0) / 120.0], dtype=np.float32)
+    return lrtei.lrtei_selector_encode(int(n), int(P))
 
 
-def decode(y: np.ndarray) -> Tuple[float, float]:
-    return 8.0 + 56.0 * float(y[0]), 8.0 + 120.0 * float(y[1])
-
-
-def molecule_features(mol) -> Tuple[float, float, float, int]:
+def molecule_features(mol) -> Tuple[float, float, int]:
     amin = min(float(np.min(s.exps)) for s in mol.shells)
     amax = max(float(np.max(s.exps)) for s in mol.shells)
     lmax = max(s.l for s in mol.shells)
@@ -68,7 +50,7 @@ def molecule_features(mol) -> Tuple[float, float, float, int]:
 
 def sweep_molecule(seed: int):
     """A random small instance spanning the feature ranges: 2-3 atoms inside an explicit box of
-    half-width 3..34 bohr, one contracted shell per atom (l up to 2), omega in [0.2, 1]."""
+    half-width 3..32 bohr, one contracted shell per atom (l up to 2), omega in [0.2, 1]."""
     rng = np.random.Generator(np.random.Philox(seed))
     half = float(np.exp(rng.uniform(np.log(3.0), np.log(32.0))))
     omega = float(rng.uniform(0.2, 1.0))
@@ -90,7 +72,13 @@ def sweep_molecule(seed: int):
     return mol, half, omega
 
 
+def sweep_indices(seed: int, nbf: int, nent: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.Philox(seed + 7))
+    return rng.integers(0, nbf, size=(nent, 4)).astype(np.int32)
+
+
 def _entries(mol, n: int, P: int, idx_dev) -> np.ndarray:
+    """Algorithm 1 entries of a fresh plan at (n, P) (lrtei_entries)."""
     import torch
     pl = lrtei.Plan(mol, "fp64", n=n, P=P)
     out = torch.empty(idx_dev.shape[0], dtype=torch.float64, device="cuda")
@@ -100,21 +88,27 @@ def _entries(mol, n: int, P: int, idx_dev) -> np.ndarray:
     return res
 
 
-def sweep(seed: int, nent: int = 96) -> dict:
+def sweep(seed: int, nent: int = 32) -> dict:
     """Errors of sampled entries at every n of N_GRID (P = P_REF) and every P of P_GRID
-    (n = N_REF), relative (Frobenius over the sample) to the entries at (N_REF, P_REF)."""
+    (n = N_REF), relative (Frobenius over the sample) to the entries at (N_REF, P_REF): one plan
+    at the reference orders, every order evaluated by lrtei_entries_orders."""
     import torch
     mol, half, omega = sweep_molecule(seed)
-    rng = np.random.Generator(np.random.Philox(seed + 7))
-    idx = rng.integers(0, mol.nbf, size=(nent, 4)).astype(np.int32)
-    idx_dev = torch.as_tensor(idx, device="cuda")
-    ref = _entries(mol, N_REF, P_REF, idx_dev)
+    idx = torch.as_tensor(sweep_indices(seed, mol.nbf, nent), device="cuda")
+    ns = N_GRID + [N_REF] * len(P_GRID) + [N_REF]
+    Ps = [P_REF] * len(N_GRID) + P_GRID + [P_REF]
+    pl = lrtei.Plan(mol, "fp64")
+    out = torch.empty((len(ns), nent), dtype=torch.float64, device="cuda")
+    lrtei.lrtei_entries_orders(pl.plan, ns, Ps, idx, nent, out)
+    res = out.cpu().numpy()
+    pl.status()
+    pl.close()
+    ref = res[-1]
     nrm = np.linalg.norm(ref)
-    err_n = [float(np.linalg.norm(_entries(mol, n, P_REF, idx_dev) - ref) / nrm) for n in N_GRID]
-    err_P = [float(np.linalg.norm(_entries(mol, N_REF, P, idx_dev) - ref) / nrm) for P in P_GRID]
+    err = [float(np.linalg.norm(r - ref) / nrm) for r in res[:-1]]
     amin, amax, lmax = molecule_features(mol)
-    return {"seed": seed, "omega": omega, "half": half, "amin": amin, "amax": amax, "lmax": lmax, "err_n": err_n,
-            "err_P": err_P}
+    return {"seed": seed, "omega": omega, "half": half, "amin": amin, "amax": amax, "lmax": lmax,
+            "err_n": err[:len(N_GRID)], "err_P": err[len(N_GRID):]}
 
 
 def label(sw: dict, target: float) -> Optional[Tuple[int, int]]:
@@ -141,13 +135,11 @@ def dataset(sweeps: Sequence[dict]):
 # ------------------------------------------------------------------ the selector object
 
 class Selector:
-    """An MLP on the GPU (library kernels) plus the fallback rule."""
+    """A handle on the library's selector (network on the GPU, policy in the library)."""
 
-    VERSION = 1
-
-    def __init__(self, hidden: int = 64, seed: int = 1):
+    def __init__(self, hidden: int = 64, seed: int = 1, handle: Optional[int] = None):
         self.hidden = hidden
-        self.handle = lrtei.lrtei_selector_create(hidden, seed)
+        self.handle = handle if handle is not None else lrtei.lrtei_selector_create(hidden, seed)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -162,13 +154,9 @@ class Selector:
 
     def train(self, X: np.ndarray, Y: np.ndarray, epochs: int = 300, batch: int = 256, lr: float = 2e-3):
         import torch
-        dX = torch.as_tensor(X, device="cuda")
-        dY = torch.as_tensor(Y, device="cuda")
-        hist = []
-        for ep in range(epochs):
-            cur = lr if ep < epochs * 2 // 3 else lr * 0.1
-            hist.append(lrtei.lrtei_selector_train_epoch(self.handle, dX, dY, len(X), batch, cur))
-        return hist
+        dX = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float32), device="cuda")
+        dY = torch.as_tensor(np.ascontiguousarray(Y, dtype=np.float32), device="cuda")
+        return list(lrtei.lrtei_selector_train(self.handle, dX, dY, len(X), epochs, batch, lr))
 
     def predict_raw(self, X: np.ndarray) -> np.ndarray:
         import torch
@@ -177,34 +165,18 @@ class Selector:
         lrtei.lrtei_selector_forward(self.handle, dX, out, len(X))
         return out.cpu().numpy()
 
-    def select(self, omega, half, amin, amax, lmax, target, margin: Tuple[int, int] = (4, 8)) -> Tuple[int, int, bool]:
-        """(n, P, used_fallback): the network's choice rounded up to the grids plus a margin, or
-        the fixed conservative (32, 48) outside the trained range."""
-        if not in_range(omega, half, amin, amax, lmax, target):
-            return FALLBACK[0], FALLBACK[1], True
-        n, P = decode(self.predict_raw(features(omega, half, amin, amax, lmax, target)[None, :])[0])
-        n = next((g for g in N_GRID + [N_MAX] if g >= n + margin[0]), N_MAX)
-        P = next((g for g in P_GRID + [P_MAX] if g >= P + margin[1]), P_MAX)
-        return int(n), int(P), False
+    def select(self, omega, half, amin, amax, lmax, target) -> Tuple[int, int, bool]:
+        """(n, P, used_fallback) from lrtei_select_np."""
+        return lrtei.lrtei_select_np(self.handle, [omega, half, amin, amax, lmax, target])
 
-    # checkpoint: versioned, with a checksum of the parameter bytes
     def save(self, path: str, meta: Optional[dict] = None):
-        params = lrtei.lrtei_selector_get_params(self.handle)
-        digest = hashlib.sha256(params.tobytes()).hexdigest()
-        header = {"version": self.VERSION, "hidden": self.hidden, "sha256": digest, "meta": meta or {}}
-        with open(path, "wb") as f:
-            np.savez(f, params=params, header=np.frombuffer(json.dumps(header).encode(), dtype=np.uint8))
+        lrtei.lrtei_selector_save(self.handle, path, json.dumps(meta or {}))
 
     @classmethod
     def load(cls, path: str) -> "Selector":
-        with open(path, "rb") as f:
-            z = np.load(io.BytesIO(f.read()))
-        header = json.loads(bytes(z["header"]).decode())
-        if header.get("version") != cls.VERSION:
-            raise ValueError(f"selector checkpoint version {header.get('version')} != {cls.VERSION}")
-        params = z["params"].astype(np.float32)
-        if hashlib.sha256(params.tobytes()).hexdigest() != header["sha256"]:
-            raise ValueError("selector checkpoint checksum mismatch")
-        sel = cls(hidden=int(header["hidden"]))
-        lrtei.lrtei_selector_set_params(sel.handle, params)
+        h, meta = lrtei.lrtei_selector_load(path)
+        npar = lrtei.lrtei_selector_nparams(h)  # H^2 + 10 H + 2 parameters for width H
+        hidden = int(round((-10 + (100 - 4 * (2 - npar)) ** 0.5) / 2))
+        sel = cls(hidden=hidden, handle=h)
+        sel.meta = json.loads(meta) if meta else {}
         return sel

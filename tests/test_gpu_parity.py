@@ -87,6 +87,60 @@ def test_factors_match_oracle(lib):
     assert row == S.shape[1]
 
 
+def mol_high_order(n, P, half, seed=2100):
+    """Two atoms with an s, a p and a d shell each (N_b = 20), exponents from 0.05 to 800, in an
+    explicit cube of half-width `half` around the atoms' centre (2.5 bohr cuts the diffuse
+    functions; 25 bohr holds them), at the Chebyshev and quadrature orders the selector reaches."""
+    m = synth.random_molecule(seed, natoms=2, cube=1.5, shells_per_atom=(("s", 1), ("p", 1), ("d", 1)), nprim=2,
+                              alpha_range=(0.05, 800.0), omega=0.6, n=n, P=P)
+    c = m.atoms.mean(axis=0)
+    m.box_lo, m.box_hi = c - half, c + half
+    return m
+
+
+@pytest.mark.parametrize("half", [2.5, 25.0])
+@pytest.mark.parametrize("n,P", [(40, 96), (56, 128), (64, 128)])
+def test_factors_and_B_rows_at_high_orders(lib, n, P, half):
+    """Nodes, weights, Chebyshev coefficients and every moment row against the oracle (pinned at
+    n = 64 by QUADPACK) at n = 40..64 and P = 96..128, and sampled rows of the FP64 B by both
+    forms within 1e-12."""
+    m = mol_high_order(n, P, half)
+    o = oracle.Oracle.from_molecule(m)
+    pl = lib.Plan(m, "fp64")
+    S, C, s, w, c = [t.cpu().numpy() for t in pl.factors()]
+    so, wo = o.nodes()
+    assert np.max(np.abs(s - so)) <= 1e-15 * m.omega
+    assert np.max(np.abs(w - wo) / wo) <= 1e-13
+    worst_c = 0.0
+    for d in range(3):
+        for p in range(m.P):
+            A = o.cheb(d, p)
+            worst_c = max(worst_c, np.max(np.abs(C[d, p] - A)) / np.abs(A).max())
+    worst_s, row = 0.0, 0
+    for mu in range(m.nbf):
+        for nu in range(mu, m.nbf):
+            Wd = [o.moments(mu, nu, d) for d in range(3)]
+            I = Wd[0].shape[0]
+            for d in range(3):
+                scale = np.abs(Wd[d]).max(axis=1)
+                worst_s = max(worst_s, float(np.max(np.abs(S[d, row:row + I] - Wd[d]).max(axis=1) / scale)))
+            row += I
+    rows = [0, 7 * m.nbf + 12, (m.nbf - 1) * m.nbf + m.nbf - 1]
+    ref = o.B_rows(rows)
+    errs = {}
+    for form in ("hadamard", "factored"):
+        B = pl.assemble_B(form)
+        errs[form] = rel_fro(B[rows].cpu().numpy(), ref)
+        del B
+    pl.status()
+    print(f"n={n} P={P} box half-width {half}: Chebyshev coefficients {worst_c:.1e}, moments {worst_s:.1e} "
+          f"(of each row's maximum), B rows {errs['hadamard']:.1e} / {errs['factored']:.1e}")
+    assert worst_c <= 1e-14
+    assert worst_s <= 1e-13
+    assert max(errs.values()) <= 1e-12
+    pl.close()
+
+
 @pytest.mark.parametrize("form", ["hadamard", "factored"])
 def test_contracted_spd_full_B_fp64(lib, form):
     m = mol_spd_small()

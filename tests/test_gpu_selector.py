@@ -1,18 +1,24 @@
 """The learned (n, P) selector: the device MLP kernels against the FP64 CPU reference network,
-training by the device Adam kernel, and the gain over the fixed (32, 48) on held-out instances.
+training by the device Adam kernel, the selection policy and checkpoints through the C ABI, and
+the selector judged by the FP64 oracle on held-out instances.
 
-Training data are error sweeps of the plain method computed by the CUDA library; the held-out
-instances are drawn with different seeds.  The measured error of the chosen (n, P) on a
-held-out instance is that of the library's entries against the library's reference order.
+Training data are error sweeps of the plain method computed by the CUDA library
+(lrtei_entries_orders); the held-out instances are drawn with other seeds.  The error of the
+chosen (n, P) on a held-out instance is that of the library's entries (a fresh plan at that
+(n, P), lrtei_entries) against the FP64 oracle's entries at the reference orders (64, 128) on the
+same sampled indices: the oracle is the judge, not the library.
 """
-import math
+import os
 
 import numpy as np
 import pytest
 
+import oracle
 from oracle import mlp as mlp_ref
 
 pytestmark = pytest.mark.gpu
+
+N_SWEEPS = int(os.environ.get("LRTEI_TEST_SELECTOR_SWEEPS", "20000"))
 
 
 @pytest.fixture(scope="module")
@@ -60,56 +66,130 @@ def test_adam_training_fits_a_smooth_map(lib):
     assert hist[-1] < 2e-3
 
 
+def test_selection_policy_through_the_c_abi(lib, tmp_path):
+    """Range check and fallback, grid rounding with margins, checkpoint round trip, and rejection
+    of a corrupted or foreign checkpoint: all inside the library."""
+    sel = lib.lrtei_selector_create(64, 9)
+    try:
+        # outside the trained ranges (omega 3, box 50 bohr, target 1e-12): the fixed (32, 48)
+        for raw in ([3.0, 10.0, 0.1, 100.0, 1, 1e-6], [0.5, 50.0, 0.1, 100.0, 1, 1e-6],
+                    [0.5, 10.0, 0.1, 100.0, 1, 1e-12], [0.5, 10.0, 0.1, 100.0, 3, 1e-6]):
+            assert lib.lrtei_select_np(sel, raw) == (32, 48, True)
+        n, P, fb = lib.lrtei_select_np(sel, [0.5, 10.0, 0.1, 100.0, 1, 1e-6])
+        assert not fb and n in (8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64) and P in (8, 12, 16, 20, 24, 28, 32, 40,
+                                                                                    48, 64, 80, 96, 128)
+        for bad in ([0.0, 10.0, 0.1, 100.0, 1, 1e-6], [0.5, 10.0, -0.1, 100.0, 1, 1e-6],
+                    [0.5, 10.0, 0.1, 100.0, 1, float("nan")]):
+            with pytest.raises(lib.LrteiError) as ei:
+                lib.lrtei_select_np(sel, bad)
+            assert ei.value.status == 1
+        f = lib.lrtei_selector_features([0.5, 12.0, 0.1, 1000.0, 2, 1e-6])
+        assert np.allclose(f, [0.5, 0.4, -1.0, 0.75, 1.0, 0.6], atol=1e-7)
+        assert np.allclose(lib.lrtei_selector_encode(64, 128), [1.0, 1.0])
+        path = str(tmp_path / "sel.bin")
+        lib.lrtei_selector_save(sel, path, '{"note": "test"}')
+        h2, meta = lib.lrtei_selector_load(path)
+        assert meta == '{"note": "test"}'
+        assert np.array_equal(lib.lrtei_selector_get_params(sel), lib.lrtei_selector_get_params(h2))
+        assert lib.lrtei_select_np(h2, [0.5, 10.0, 0.1, 100.0, 1, 1e-6]) == (n, P, False)
+        lib.lrtei_selector_destroy(h2)
+        raw = bytearray(open(path, "rb").read())
+        raw[40] ^= 1
+        bad = str(tmp_path / "bad.bin")
+        open(bad, "wb").write(bytes(raw))
+        with pytest.raises(lib.LrteiError) as ei:
+            lib.lrtei_selector_load(bad)
+        assert "checksum" in str(ei.value)
+        raw = bytearray(open(path, "rb").read())
+        raw[8] = 7  # another version
+        open(bad, "wb").write(bytes(raw))
+        with pytest.raises(lib.LrteiError) as ei:
+            lib.lrtei_selector_load(bad)
+        assert "version" in str(ei.value)
+    finally:
+        lib.lrtei_selector_destroy(sel)
+
+
+def test_sweep_orders_match_fresh_plans(lib):
+    """lrtei_entries_orders (one plan, moments shared across n) against a fresh plan per (n, P)."""
+    import torch
+    from paper_2210_13069_gb300 import selector as S
+    mol, _, _ = S.sweep_molecule(123)
+    idx = torch.as_tensor(S.sweep_indices(123, mol.nbf, 40), device="cuda")
+    ns, Ps = [8, 24, 56, 64, 64], [128, 128, 128, 12, 128]
+    pl = lib.Plan(mol, "fp64")
+    out = torch.empty((len(ns), 40), dtype=torch.float64, device="cuda")
+    lib.lrtei_entries_orders(pl.plan, ns, Ps, idx, 40, out)
+    got = out.cpu().numpy()
+    pl.status()
+    pl.close()
+    for k, (n, P) in enumerate(zip(ns, Ps)):
+        ref = S._entries(mol, n, P, idx)
+        assert np.max(np.abs(got[k] - ref)) <= 1e-13 * np.abs(ref).max(), (n, P)
+
+
 @pytest.fixture(scope="module")
 def trained(lib):
-    """The selector trained on 160 error sweeps (about a minute on the GPU)."""
+    """The selector trained on N_SWEEPS error sweeps of the plain method."""
+    import time
     from paper_2210_13069_gb300 import selector as S
-    train = [S.sweep(10_000 + i) for i in range(160)]
+    t0 = time.perf_counter()
+    train = [S.sweep(10_000 + i) for i in range(N_SWEEPS)]
+    t1 = time.perf_counter()
     X, Y = S.dataset(train)
-    assert len(X) > 400
+    assert len(X) > 2 * N_SWEEPS
     sel = S.Selector(64, seed=11)
-    hist = sel.train(X, Y, epochs=250, batch=256, lr=2e-3)
+    epochs = 250 if N_SWEEPS <= 500 else 60
+    hist = sel.train(X, Y, epochs=epochs, batch=256, lr=2e-3)
+    t2 = time.perf_counter()
+    print(f"selector: {N_SWEEPS} sweeps in {t1 - t0:.1f} s, {len(X)} labelled rows, {epochs} epochs in {t2 - t1:.1f} s, "
+          f"loss {hist[0]:.2e} -> {hist[-1]:.2e}")
     assert hist[-1] < hist[0]
     return sel, X, train
 
 
-def test_selector_meets_target_and_gains_over_fixed(lib, trained, tmp_path):
-    """On held-out instances: the chosen (n, P) reaches the requested error in at least 90 % of
-    the reachable cases, and where the fixed (32, 48) also reaches it the chosen one is cheaper
-    on average (cost ~ n^3 per J-build)."""
+def test_selector_meets_target_judged_by_the_oracle(lib, trained):
+    """Held-out instances: the chosen (n, P) reaches the requested error against the FP64
+    oracle's entries at (64, 128) in at least 90 % of the cases where the plain method can reach
+    it, and where the fixed (32, 48) also reaches it the chosen one is cheaper on average (cost of
+    a J-build ~ n^3)."""
     import torch
     from paper_2210_13069_gb300 import selector as S
-    sel, X, train = trained
+    sel, _, _ = trained
     met = tried = 0
-    gains, fixed_fail = [], 0
-    for i in range(16):
-        sw = S.sweep(90_000 + i)
+    gains, fixed_fail, worst = [], 0, 0.0
+    for i in range(24):
+        seed = 90_000 + i
+        mol, half, omega = S.sweep_molecule(seed)
+        idx_h = S.sweep_indices(seed, mol.nbf, 96)
+        idx = torch.as_tensor(idx_h, device="cuda")
+        ref = oracle.Oracle.from_molecule(mol, n=S.N_REF, P=S.P_REF).entries(idx_h)  # the judge
+        nrm = np.linalg.norm(ref)
+        amin, amax, lmax = S.molecule_features(mol)
+        err_at = {}
+
+        def err(n, P):
+            if (n, P) not in err_at:
+                err_at[(n, P)] = float(np.linalg.norm(S._entries(mol, n, P, idx) - ref) / nrm)
+            return err_at[(n, P)]
+
         for t in (1e-4, 1e-6, 1e-8):
-            if S.label(sw, t) is None:
+            if err(56, 96) > t / 4:  # the plain method's grid cannot reach t on this instance
                 continue
-            n, P, fb = sel.select(sw["omega"], sw["half"], sw["amin"], sw["amax"], sw["lmax"], t)
-            mol, _, _ = S.sweep_molecule(90_000 + i)
-            rng = np.random.Generator(np.random.Philox(90_000 + i + 7))
-            idx = torch.as_tensor(rng.integers(0, mol.nbf, size=(96, 4)).astype(np.int32), device="cuda")
-            ref = S._entries(mol, S.N_REF, S.P_REF, idx)
-            err = float(np.linalg.norm(S._entries(mol, n, P, idx) - ref) / np.linalg.norm(ref))
-            err_fixed = float(np.linalg.norm(S._entries(mol, 32, 48, idx) - ref) / np.linalg.norm(ref))
+            n, P, fb = sel.select(omega, half, amin, amax, lmax, t)
+            e = err(n, P)
             tried += 1
-            met += err <= t
-            if err_fixed <= t:
+            met += e <= t
+            worst = max(worst, e / t)
+            if err(*S.FALLBACK) <= t:
                 gains.append((32 ** 3) / (n ** 3))
             else:
                 fixed_fail += 1
-    print(f"selector: met {met}/{tried}; fixed (32,48) failed {fixed_fail}/{tried}; "
-          f"mean cost gain where both meet the target {np.mean(gains):.2f}x")
+    print(f"selector judged by the oracle: met {met}/{tried}; fixed (32, 48) failed {fixed_fail}/{tried}; "
+          f"mean cost gain where both meet the target {np.mean(gains):.2f}x; worst error / target {worst:.2f}")
+    assert tried >= 40
     assert met >= 0.9 * tried
     assert np.mean(gains) > 1.0
-    # checkpoint round trip
-    p = str(tmp_path / "sel.npz")
-    sel.save(p, meta={"sweeps": len(train)})
-    sel2 = S.Selector.load(p)
-    assert np.array_equal(sel.predict_raw(X[:50]), sel2.predict_raw(X[:50]))
-
 
 
 def test_selector_on_a_600_function_molecule(lib, trained):
@@ -132,7 +212,7 @@ def test_selector_on_a_600_function_molecule(lib, trained):
     probe.close()
     n_sel, P_sel, fb = sel.select(m.omega, half, amin, amax, lmax, target)
     assert not fb, "the 600-function molecule lies inside the trained feature ranges"
-    n_ref, P_ref = min(max(n_sel, 32) + 8, 72), max(P_sel, 48) + 16
+    n_ref, P_ref = min(max(n_sel, 32) + 8, 64), max(P_sel, 48) + 16
     D = torch.as_tensor(synth.random_densities(600, m.nbf, R), device="cuda")
 
     def jbuild(prec, n, P):

@@ -154,6 +154,29 @@ def test_moments_match_scipy_quad():
             assert np.max(np.abs(W[j] - ref)) <= 1e-12 * scale + 1e-300
 
 
+@pytest.mark.parametrize("half", [2.5, 25.0])
+def test_moments_match_scipy_quad_high_order(half):
+    """The same at the highest orders the library takes (n = 64, T_63 oscillating across the box),
+    in a small box that cuts diffuse functions and in a large one, with exponents from 0.05 to 800."""
+    centers = ((0.0, 0.3, -0.2), (0.8, -0.6, 0.5))
+    box = ((-half, -half, -half), (half, half, half))
+    o = small_mol(ls=(2, 1), nprim=(2, 2), exps=(800.0, 0.05, 3.0, 0.3), coefs=(0.5, 0.5, 0.7, 0.3),
+                  centers=centers, n=64, P=2, box=box)
+    rng = np.random.default_rng(7)
+    checked = 0
+    for _ in range(3):
+        mu, nu = (int(x) for x in rng.integers(0, o.nbf, 2))
+        d = int(rng.integers(0, 3))
+        W = o.moments(mu, nu, d)
+        k2 = len(o.basis_function(nu)[2])
+        for j in range(W.shape[0]):
+            ref = quad_moment(o, mu, nu, d, j // k2, j % k2)
+            scale = np.max(np.abs(ref))
+            assert np.max(np.abs(W[j] - ref)) <= 1e-12 * scale, (mu, nu, d, j)
+            checked += 1
+    assert checked >= 6
+
+
 def test_moments_closed_form_inside_box():
     """A Gaussian pair deep inside the box: int e^{-p(x-P)^2} K_AB T_m((x-c)/b) for m = 0, 1, 2
     equals K_AB sqrt(pi/p) (1, (P-c)/b, 2((P-c)^2 + 1/(2p))/b^2 - 1)."""
