@@ -92,6 +92,8 @@ typedef struct {
   double tau_screening;   /* primitive-pair screening threshold of the plan (0: none) */
   int cheb_n;       /* Chebyshev nodes per dimension the plan was created with */
   int kr_rank;      /* 0, or the rank R after lrtei_plan_compress (then n == R) */
+  int npartitions;  /* 0, or the number of adaptive-box partitions (lrtei_plan_create_adaptive) */
+  double partition_b[8]; /* their cubes' half-widths b_s, ascending (the box above is the largest) */
 } lrtei_plan_info;
 
 /* ---- basis (Section 1, eq. "basis"/"primi") ------------------------------------------
@@ -119,6 +121,25 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
 lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
                                   const double* box_hi, lrtei_precision precision, double tau_screening,
                                   void* stream, lrtei_plan** out);
+/* Adaptive choice of the integration domain (Section 6, "Adaptive approach for the choice of the
+ * integration domain"; paper's tau_adaptive = 1e-20).  The numerical support of a primitive pair
+ * j in dimension l is |x_l - P_{j,l}| < sqrt(ln(1/tau_adaptive) / p_j) (where its Gaussian factor
+ * exceeds tau_adaptive); a unique basis pair's support is the smallest cube about the centre c of
+ * the atoms' extent holding those of all its primitive pairs.  The pairs, sorted by that half-width
+ * (stable), are cut into npartitions groups of about equal count (a cut never splits pairs of equal
+ * support, so the Cartesian components of one shell pair stay together; empty groups are dropped);
+ * partition s is the cube [c - b_s, c + b_s]^3, b_s the largest support of its group.  A pair's
+ * moments are integrated over its partition's cube (eq. defV on that cube), and between partitions
+ * s and t the kernel is interpolated on the two cubes' first-kind Chebyshev grids:
+ *   A^(p)_{st}(a, b) = c_a c_b / n^2 sum_{k,k'} exp(-s_p^2 (b_s u_k - b_t u_k')^2) T_a(u_k) T_b(u_k'),
+ * B(mu nu, ka la) = (w/sqrt(pi)) sum_p w_p sum_{j,j'} c_j c_j' prod_d (S_d(j) A^(p)_{st,d} S_d(j')^T).
+ * One n serves every partition.  Supported on the plan: lrtei_assemble_B (partition blocks
+ * B_st = F_s K_st F_t^T: tensor cores for the split precisions, FP64 mode products otherwise; into
+ * device memory or mapped pinned memory), lrtei_entries, lrtei_jbuild (FP64 for every precision),
+ * lrtei_factors (d_C then holds npartitions^2 blocks, index (s npartitions + t), each 3 x P x n x n).
+ * Other calls return LRTEI_ERR_UNSUPPORTED.  tau_adaptive in (0, 1), npartitions in 1..8. */
+lrtei_status lrtei_plan_create_adaptive(const lrtei_basis* basis, double omega, int n, int P, double tau_adaptive,
+                                        int npartitions, lrtei_precision precision, void* stream, lrtei_plan** out);
 void lrtei_plan_destroy(lrtei_plan* plan);
 lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info);
 /* Synchronises the plan's stream and returns the latched device-side status (then clears it). */
@@ -220,6 +241,19 @@ lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream);
  * kernel by kernel.  The environment switches are read when a call is made; a replayed graph
  * keeps the choices of the call it was captured from. */
 lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream);
+
+/* ---- long-range exchange (appendix "The Hartree-Fock exchange", eq. exchange) -------------
+ * K^lr(mu, nu) = 2 sum_j sum_{la, ka} q_{j la} q_{j ka} B(mu la, ka nu) for the orbital
+ * coefficients d_Q (device, norb x N_b, row-major) into d_K (device, N_b x N_b, row-major),
+ * without forming B: through the factored form, K^lr = 2 sum_j X_j K X_j^T with
+ * X_j(mu, :) = sum_la q_{j la} M(mu la, :) (M of eq. tensors, K = (w/sqrt(pi)) sum_p w_p
+ * (x)_d A_d^(p)).  Orbitals are processed in blocks (X of a block within ~1 GiB;
+ * LRTEI_EXCHANGE_BLOCK=<orbitals> in the environment sets the block).  Tensor-core
+ * precisions run the three products on tcgen05 with split operands; FP64 / FP32 plans run FP64
+ * CUDA-core GEMMs and apply K by mode products (eq. ig1).  A compressed plan gives eq.
+ * approxepsilon's exchange.  Device scratch ~6 x min(norb, block) N_b n^3 doubles plus N_b^2 n^3
+ * (and their slices).  LRTEI_ERR_ARG for NULL pointers or norb <= 0. */
+lrtei_status lrtei_exchange(lrtei_plan* plan, const double* d_Q, int norb, double* d_K, void* stream);
 
 /* ---- batched J-builds (many molecules of uneven size in one graph-captured launch) -------
  * plans[nmol]: plans (each with its own omega, n, P); d_D[m], d_J[m], R[m]: per-molecule

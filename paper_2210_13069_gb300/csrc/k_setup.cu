@@ -69,13 +69,17 @@ void launch_nodes_map(int P, double omega, const double* d_z, double* d_s, cudaS
 // ---------------------------------------------------------------- Chebyshev coefficients ----
 // One block per (d, p).  With Tm(a, k) = T_a(u_k) = cos(a (2k+1) pi / (2n)) and
 // F(k, k') = exp(-(s_p b_d)^2 (u_k - u_k')^2), alpha = (c_ab / n^2) (Tm F Tm^T)(a, b).
-__global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3, double* C) {
+// Two intervals (the adaptive boxes of Section 6): x = c + hx_d u on one side, y = c + hy_d v on
+// the other, F(k, k') = exp(-s_p^2 (hx_d u_k - hy_d u_k')^2); hy3 == NULL means hy3 = hx3.
+__global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3, const double* hy3, double* C) {
   extern __shared__ double sm[];
   double* Tm = sm;          // n x n
   double* G = sm + n * n;   // n x n : G(k, b) = sum_k' F(k, k') Tm(b, k')
   const int d = blockIdx.x / P, p = blockIdx.x % P;
   const double pi = 3.141592653589793238;
   const double sb = s[p] * half3[d];
+  const bool cross = hy3 != nullptr && hy3[d] != half3[d];
+  const double hx = half3[d], hy = cross ? hy3[d] : hx;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int a = t / n, k = t % n;
     Tm[t] = cos(a * (2.0 * k + 1.0) * pi / (2.0 * n));
@@ -87,7 +91,7 @@ __global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3,
     double acc = 0.0;
     for (int kk = 0; kk < n; ++kk) {
       const double vk = cos((2.0 * kk + 1.0) * pi / (2.0 * n));
-      double df = sb * (uk - vk);
+      double df = cross ? s[p] * (hx * uk - hy * vk) : sb * (uk - vk);
       acc += exp(-df * df) * Tm[b * n + kk];
     }
     G[t] = acc;
@@ -108,7 +112,15 @@ void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, d
   size_t smem = 2 * sizeof(double) * n * n;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   count_launch();
-  k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_half3, d_C);
+  k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_half3, nullptr, d_C);
+}
+
+void launch_cheb_coeff_cross(int n, int P, const double* d_s, const double* d_hx3, const double* d_hy3, double* d_C,
+                             cudaStream_t st) {
+  size_t smem = 2 * sizeof(double) * n * n;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launch();
+  k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_hx3, d_hy3, d_C);
 }
 
 // ------------------------------------------------------------------ normalisation ----
@@ -213,8 +225,8 @@ template <int NM>
 __global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const double* row_p, const double* row_P,
                                                  const double* row_K, const double* row_A, const double* row_B,
                                                  const int8_t* row_pa, const int8_t* row_pb, const double* lo3,
-                                                 const double* hi3, const double* gz, const double* gw,
-                                                 const int64_t* rep, int64_t nitems, double* S) {
+                                                 const double* hi3, const uint8_t* row_box, const double* gz,
+                                                 const double* gw, const int64_t* rep, int64_t nitems, double* S) {
   __shared__ double red[4][32][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t item = (int64_t)blockIdx.x * 4 + warp;
@@ -231,7 +243,8 @@ __global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const dou
     const double Pc = row_P[d * nrows + row], K = row_K[d * nrows + row];
     const double A = row_A[d * nrows + row], B = row_B[d * nrows + row];
     const int ia = row_pa[d * nrows + row], ib = row_pb[d * nrows + row];
-    const double lo = lo3[d], hi = hi3[d];
+    const int box = row_box ? (int)row_box[row] : 0;  // adaptive boxes: the row's partition
+    const double lo = lo3[3 * box + d], hi = hi3[3 * box + d];
     const double cen = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
     const double reach = 9.0 / sqrt(p);
     const double wl = fmax(lo, Pc - reach), wh = fmin(hi, Pc + reach);
@@ -328,8 +341,9 @@ void launch_gather_moments(int64_t count, int n, const int* d_key, const double*
   k_gather_moments<<<(unsigned)blocks, 256, 0, st>>>(count, n, d_key, d_Su, d_S);
 }
 
-void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const double* d_gz,
-                    const double* d_gw, const int64_t* d_rep, int64_t nitems, double* d_S, cudaStream_t st) {
+void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const uint8_t* d_row_box,
+                    const double* d_gz, const double* d_gw, const int64_t* d_rep, int64_t nitems, double* d_S,
+                    cudaStream_t st) {
   if (nitems <= 0) return;
   const int64_t items = nitems;
   const unsigned blocks = (unsigned)((items + 3) / 4);
@@ -337,7 +351,7 @@ void launch_moments(const PairTable& t, int n, const double* d_lo3, const double
   // accumulators for n rounded up to a multiple of 8 (the recurrence costs two FMAs per term)
 #define LRTEI_MOMENTS(NM)                                                                                       \
   k_moments<NM><<<blocks, 128, 0, st>>>(t.nrows, n, t.row_p, t.row_P, t.row_K, t.row_A, t.row_B, t.row_pa, t.row_pb, \
-                                        d_lo3, d_hi3, d_gz, d_gw, d_rep, nitems, d_S)
+                                        d_lo3, d_hi3, d_row_box, d_gz, d_gw, d_rep, nitems, d_S)
   switch ((n + 7) / 8) {
     case 1: LRTEI_MOMENTS(8); break;
     case 2: LRTEI_MOMENTS(16); break;

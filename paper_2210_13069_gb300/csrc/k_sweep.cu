@@ -76,6 +76,10 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
   PlanView v;
   lrtei_status s = plan_view(plan, &v);
   if (s != LRTEI_OK) return s;
+  if (v.npart > 0) {
+    set_error("lrtei_entries_orders: adaptive-box plans are not supported");
+    return LRTEI_ERR_UNSUPPORTED;
+  }
   if (v.kr_rank > 0) {
     set_error("lrtei_entries_orders: the plan's moments are compressed; sweeps need the uncompressed ones");
     return LRTEI_ERR_UNSUPPORTED;

@@ -58,6 +58,14 @@ struct lrtei_plan {
   lrtei_precision prec = LRTEI_FP64;
   double tau = 0.0;  // primitive-pair screening threshold
   int last_form = 0;
+  // adaptive boxes (Section 6): 0 partitions = one box for every pair
+  int npart = 0;
+  double tau_adapt = 0.0;
+  std::vector<int> h_pair_part;        // partition of each unique pair
+  std::vector<double> part_b;          // half-width of each partition's cube
+  double adapt_c[3] = {0.0, 0.0, 0.0}; // the cubes' common centre
+  int* d_pair_part = nullptr;
+  uint8_t* d_row_box = nullptr;        // partition of each primitive-pair row (moments' box)
   int cheb_n = 0;         // Chebyshev nodes per dimension (n before a Khatri-Rao compression)
   int kr_rank = 0;        // 0, or the common rank R of the compressed moment matrices (n == R then)
   int kr_ranks[3] = {0, 0, 0};
@@ -186,9 +194,32 @@ lrtei_status lrtei_plan_create(const lrtei_basis* basis, double omega, int n, in
   return lrtei_plan_create_ex(basis, omega, n, P, box_lo, box_hi, precision, 0.0, stream, out);
 }
 
+static lrtei_status plan_create_impl(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
+                                     const double* box_hi, lrtei_precision precision, double tau_screening,
+                                     double tau_adapt, int npart, void* stream, lrtei_plan** out);
+
 lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
                                   const double* box_hi, lrtei_precision precision, double tau_screening,
                                   void* stream, lrtei_plan** out) {
+  return plan_create_impl(basis, omega, n, P, box_lo, box_hi, precision, tau_screening, 0.0, 0, stream, out);
+}
+
+lrtei_status lrtei_plan_create_adaptive(const lrtei_basis* basis, double omega, int n, int P, double tau_adaptive,
+                                        int npartitions, lrtei_precision precision, void* stream, lrtei_plan** out) {
+  if (!out) { set_error("out is NULL"); return LRTEI_ERR_ARG; }
+  if (!(tau_adaptive > 0.0 && tau_adaptive < 1.0)) {
+    set_error("tau_adaptive must be in (0, 1) (got %g)", tau_adaptive);
+    return LRTEI_ERR_ARG;
+  }
+  if (npartitions < 1 || npartitions > 8) { set_error("npartitions must be in 1..8 (got %d)", npartitions); return LRTEI_ERR_ARG; }
+  return plan_create_impl(basis, omega, n, P, nullptr, nullptr, precision, 0.0, tau_adaptive, npartitions, stream, out);
+}
+
+}  // extern "C"
+
+static lrtei_status plan_create_impl(const lrtei_basis* basis, double omega, int n, int P, const double* box_lo,
+                                     const double* box_hi, lrtei_precision precision, double tau_screening,
+                                     double tau_adapt, int npart, void* stream, lrtei_plan** out) {
   if (!out) { set_error("out is NULL"); return LRTEI_ERR_ARG; }
   if (!(tau_screening >= 0.0 && tau_screening <= 1.0)) {
     set_error("tau_screening must be in [0, 1] (got %g)", tau_screening);
@@ -249,6 +280,64 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   const int nbf = b.nbf;
   PairTable& t = pl->t;
   t.npair = npair_of(nbf);
+  if (npart > 0) {
+    // Adaptive boxes (Section 6): the support of a unique pair is the smallest cube about the
+    // centre c of the atoms' extent holding |x_l - P_{j,l}| < sqrt(ln(1/tau) / p_j) for all its
+    // primitive pairs j and dimensions l; the pairs sorted by it (stable) are cut into npart groups
+    // of about equal count, each cut moved past a run of equal supports, empty groups dropped.
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300}, c[3];
+    for (int s2 = 0; s2 < b.nshells; ++s2)
+      for (int d = 0; d < 3; ++d) {
+        mn[d] = std::min(mn[d], b.centers[3 * s2 + d]);
+        mx[d] = std::max(mx[d], b.centers[3 * s2 + d]);
+      }
+    for (int d = 0; d < 3; ++d) c[d] = 0.5 * (mn[d] + mx[d]);
+    const double lr = log(1.0 / tau_adapt);
+    std::vector<double> bsup((size_t)t.npair);
+    int64_t r = 0;
+    for (int mu = 0; mu < nbf; ++mu)
+      for (int nu = mu; nu < nbf; ++nu, ++r) {
+        const int s1 = b.bf_shell[mu], s2 = b.bf_shell[nu];
+        double bb = 0.0;
+        for (int j1 = 0; j1 < b.nprim[s1]; ++j1)
+          for (int j2 = 0; j2 < b.nprim[s2]; ++j2) {
+            const double a = b.exps[b.poff[s1] + j1], e = b.exps[b.poff[s2] + j2], p = a + e;
+            double m = 0.0;
+            for (int d = 0; d < 3; ++d)
+              m = std::max(m, fabs((a * b.centers[3 * s1 + d] + e * b.centers[3 * s2 + d]) / p - c[d]));
+            bb = std::max(bb, m + sqrt(lr / p));
+          }
+        bsup[r] = bb;
+      }
+    std::vector<int64_t> order((size_t)t.npair);
+    for (int64_t i = 0; i < t.npair; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return bsup[x] < bsup[y]; });
+    std::vector<int64_t> cuts{0};
+    for (int k = 1; k < npart; ++k) {
+      int64_t ct = std::max(cuts.back(), (int64_t)k * t.npair / npart);
+      while (ct > 0 && ct < t.npair && bsup[order[ct]] == bsup[order[ct - 1]]) ++ct;
+      cuts.push_back(ct);
+    }
+    cuts.push_back(t.npair);
+    pl->h_pair_part.assign((size_t)t.npair, 0);
+    for (int k = 0; k < npart; ++k) {
+      if (cuts[k + 1] <= cuts[k]) continue;
+      double bmax = 0.0;
+      for (int64_t i = cuts[k]; i < cuts[k + 1]; ++i) {
+        pl->h_pair_part[order[i]] = (int)pl->part_b.size();
+        bmax = std::max(bmax, bsup[order[i]]);
+      }
+      pl->part_b.push_back(bmax);
+    }
+    pl->npart = (int)pl->part_b.size();
+    pl->tau_adapt = tau_adapt;
+    for (int d = 0; d < 3; ++d) pl->adapt_c[d] = c[d];
+    for (int d = 0; d < 3; ++d) {  // the reported box is the largest partition's
+      pl->lo[d] = c[d] - pl->part_b.back();
+      pl->hi[d] = c[d] + pl->part_b.back();
+    }
+  }
+  const int nbox = std::max(1, pl->npart);
   // Rows are the primitive pairs (j1, j2) of each unique pair, j1 of mu's shell major; with
   // screening (Section 6) a primitive pair with exp(-a b / (a + b) |A - B|^2) <= tau is left out.
   std::vector<int> pmu(t.npair), pnu(t.npair), pI(t.npair);
@@ -296,10 +385,14 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   PA(pl->d_w, P);
   PA(pl->d_gz, kMomentPts);
   PA(pl->d_gw, kMomentPts);
-  PA(pl->d_lo3, 3);
-  PA(pl->d_hi3, 3);
-  PA(pl->d_half3, 3);
-  PA(pl->d_C, (size_t)3 * P * n * n);
+  PA(pl->d_lo3, 3 * nbox);
+  PA(pl->d_hi3, 3 * nbox);
+  PA(pl->d_half3, 3 * nbox);
+  PA(pl->d_C, (size_t)nbox * nbox * 3 * P * n * n);
+  if (pl->npart > 0) {
+    PA(pl->d_pair_part, t.npair);
+    PA(pl->d_row_box, t.nrows);
+  }
   PA(pl->d_S, (size_t)3 * t.nrows * n);
   PA(pl->d_status, 1);
   PA(t.pair_mu, t.npair);
@@ -317,8 +410,19 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   PA(t.row_pb, 3 * t.nrows);
   PA(t.row_prim, t.nrows);
 #undef PA
-  double half3[3];
-  for (int d = 0; d < 3; ++d) half3[d] = 0.5 * (pl->hi[d] - pl->lo[d]);
+  std::vector<double> lo3(3 * (size_t)nbox), hi3(3 * (size_t)nbox), half3(3 * (size_t)nbox);
+  for (int k = 0; k < nbox; ++k)
+    for (int d = 0; d < 3; ++d) {
+      lo3[3 * k + d] = pl->npart > 0 ? pl->adapt_c[d] - pl->part_b[k] : pl->lo[d];
+      hi3[3 * k + d] = pl->npart > 0 ? pl->adapt_c[d] + pl->part_b[k] : pl->hi[d];
+      half3[3 * k + d] = 0.5 * (hi3[3 * k + d] - lo3[3 * k + d]);
+    }
+  std::vector<uint8_t> row_box;
+  if (pl->npart > 0) {
+    row_box.resize((size_t)t.nrows);
+    for (int64_t r2 = 0; r2 < t.npair; ++r2)
+      for (int64_t j = prow[r2]; j < prow[r2 + 1]; ++j) row_box[j] = (uint8_t)pl->h_pair_part[r2];
+  }
 #define UP(dst, src, cnt)                                                                                 \
   if ((ce = cudaMemcpyAsync((dst), (src), sizeof(*(src)) * (cnt), cudaMemcpyHostToDevice, st)) != cudaSuccess) { \
     delete pl;                                                                                            \
@@ -332,9 +436,13 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   UP(pl->d_shell_center, b.centers.data(), 3 * b.nshells);
   UP(pl->d_exps, b.exps.data(), b.exps.size());
   UP(pl->d_coefs, b.coefs.data(), b.coefs.size());
-  UP(pl->d_lo3, pl->lo, 3);
-  UP(pl->d_hi3, pl->hi, 3);
-  UP(pl->d_half3, half3, 3);
+  UP(pl->d_lo3, lo3.data(), 3 * nbox);
+  UP(pl->d_hi3, hi3.data(), 3 * nbox);
+  UP(pl->d_half3, half3.data(), 3 * nbox);
+  if (pl->npart > 0) {
+    UP(pl->d_pair_part, pl->h_pair_part.data(), t.npair);
+    if (t.nrows > 0) UP(pl->d_row_box, row_box.data(), t.nrows);
+  }
   UP(t.pair_mu, pmu.data(), t.npair);
   UP(t.pair_nu, pnu.data(), t.npair);
   UP(t.pair_row, prow.data(), t.npair + 1);
@@ -351,7 +459,14 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   launch_gauss_legendre(P, pl->d_z, pl->d_w, st);
   launch_nodes_map(P, omega, pl->d_z, pl->d_s, st);
   launch_gauss_legendre(kMomentPts, pl->d_gz, pl->d_gw, st);
-  launch_cheb_coeff(n, P, pl->d_s, pl->d_half3, pl->d_C, st);
+  if (pl->npart == 0) {
+    launch_cheb_coeff(n, P, pl->d_s, pl->d_half3, pl->d_C, st);
+  } else {  // one coefficient block per ordered partition pair (s, t): x in box s, y in box t
+    for (int s1 = 0; s1 < nbox; ++s1)
+      for (int s2 = 0; s2 < nbox; ++s2)
+        launch_cheb_coeff_cross(n, P, pl->d_s, pl->d_half3 + 3 * s1, pl->d_half3 + 3 * s2,
+                                pl->d_C + (size_t)(s1 * nbox + s2) * 3 * P * n * n, st);
+  }
   // Moments of the distinct keys (shell pair, primitive pair, d, powers in d) only, gathered into
   // the rows afterwards: rows that share a key have identical inputs, so S is the same as computed
   // row by row (about half the work for an s/p/d basis).
@@ -366,7 +481,7 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
       }
     if (nkeys >= (int64_t)INT32_MAX) {  // keys are 32-bit: compute every row's moments directly
       ProfScope ps("moments", st);
-      launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_gz, pl->d_gw, nullptr, 3 * t.nrows, pl->d_S, st);
+      launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_row_box, pl->d_gz, pl->d_gw, nullptr, 3 * t.nrows, pl->d_S, st);
     } else {
       int* d_key = nullptr;
       int* d_l = nullptr;
@@ -393,7 +508,7 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
       launch_moment_keys(t, pl->d_bf_shell, pl->d_bf_pow, pl->d_shell_nprim, d_l, d_off, ns, d_key, d_rep, st);
       {
         ProfScope ps("moments", st);
-        launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_gz, pl->d_gw, d_rep, nkeys, d_Su, st);
+        launch_moments(t, n, pl->d_lo3, pl->d_hi3, pl->d_row_box, pl->d_gz, pl->d_gw, d_rep, nkeys, d_Su, st);
       }
       launch_gather_moments(3 * t.nrows, n, d_key, d_Su, pl->d_S, st);
       if ((s = fin(cudaGetLastError(), "moment kernels")) != LRTEI_OK) return s;
@@ -403,6 +518,8 @@ lrtei_status lrtei_plan_create_ex(const lrtei_basis* basis, double omega, int n,
   *out = pl;
   return LRTEI_OK;
 }
+
+extern "C" {
 
 void lrtei_plan_destroy(lrtei_plan* plan) {
   if (!plan) return;
@@ -426,6 +543,8 @@ lrtei_status lrtei_plan_info_get(const lrtei_plan* plan, lrtei_plan_info* info) 
   info->tau_screening = plan->tau;
   info->cheb_n = plan->cheb_n;
   info->kr_rank = plan->kr_rank;
+  info->npartitions = plan->npart;
+  for (int k = 0; k < 8; ++k) info->partition_b[k] = k < plan->npart ? plan->part_b[k] : 0.0;
   return LRTEI_OK;
 }
 
@@ -799,6 +918,171 @@ static lrtei_status assemble_B_host_banded(lrtei_plan* pl, double* hB, int64_t l
   return status;  // the last band ends at npair, so every row of B has been written
 }
 
+// ---- adaptive boxes (Section 6): partition blocks of the factored form -----------------------
+// Rows of F_u regrouped by partition (partition s occupies rows [off[s], off[s+1]) of Fp) and the
+// matching unique-pair indices (d_idx, same order).
+struct AdaptiveRows {
+  std::vector<int64_t> off;
+  int64_t* d_idx = nullptr;
+  double* Fp = nullptr;
+};
+
+lrtei_status adaptive_rows(lrtei_plan* pl, Scratch& sc, AdaptiveRows& ar, bool with_F, cudaStream_t st) {
+  const int np = pl->npart;
+  const int64_t npair = pl->t.npair, n3 = (int64_t)pl->n * pl->n * pl->n;
+  std::vector<int64_t> idx;
+  ar.off.assign(1, 0);
+  for (int s = 0; s < np; ++s) {
+    for (int64_t r = 0; r < npair; ++r)
+      if (pl->h_pair_part[r] == s) idx.push_back(r);
+    ar.off.push_back((int64_t)idx.size());
+  }
+  LRTEI_TRY(sc.get(&ar.d_idx, (size_t)npair));
+  LRTEI_CUDA(cudaMemcpyAsync(ar.d_idx, idx.data(), sizeof(int64_t) * npair, cudaMemcpyHostToDevice, st));
+  if (with_F) {
+    LRTEI_TRY(ensure_F64(pl, st));
+    LRTEI_TRY(sc.get(&ar.Fp, (size_t)npair * n3));
+    launch_gather_rows(pl->d_F, ar.d_idx, npair, n3, ar.Fp, st);
+  }
+  // the host index list is read by the copy above before this function returns
+  LRTEI_CUDA(cudaStreamSynchronize(st));
+  return LRTEI_OK;
+}
+
+// B_u of an adaptive plan: B_{st} = F_s K_{st} F_t^T for s <= t, scattered (and mirrored) into Bu.
+// K_{st} is applied as G = F_s K_{st} (rows of G = K_{ts} applied to rows of F_s): by three mode
+// products per node with A_{ts} (FP64 / FP32 plans), or densely on the tensor cores.
+lrtei_status bu_adaptive(lrtei_plan* pl, double* Bu, cudaStream_t st) {
+  const int np = pl->npart, n = pl->n, P = pl->P;
+  const int64_t npair = pl->t.npair, n3 = (int64_t)n * n * n;
+  const size_t cblk = (size_t)3 * P * n * n;
+  const double pref = pl->omega / sqrt(kPi);
+  Scratch sc(st);
+  AdaptiveRows ar;
+  LRTEI_TRY(adaptive_rows(pl, sc, ar, true, st));
+  int64_t maxr = 0;
+  for (int s = 0; s < np; ++s) maxr = std::max(maxr, ar.off[s + 1] - ar.off[s]);
+  double *G, *blk;
+  LRTEI_TRY(sc.get(&G, (size_t)maxr * n3));
+  LRTEI_TRY(sc.get(&blk, (size_t)maxr * maxr));
+  if (is_split(pl)) {
+    SplitMatrix Fsp, Ksp, Gsp;
+    LRTEI_TRY(scratch_split(sc, Fsp, npair, n3, true, pl));
+    LRTEI_TRY(scratch_split(sc, Ksp, n3, n3, true, pl));
+    LRTEI_TRY(scratch_split(sc, Gsp, maxr, n3, false, pl));
+    double* K;
+    LRTEI_TRY(sc.get(&K, (size_t)n3 * n3));
+    {
+      ProfScope ps("split", st);
+      launch_split_rows(ar.Fp, npair, n3, n3, Fsp, true, nslices(pl), st);
+    }
+    auto rows_of = [&](int s) {  // row view of partition s
+      SplitMatrix v = Fsp;
+      const int64_t r0 = ar.off[s];
+      v.rows = ar.off[s + 1] - r0;
+      v.s0 += r0 * v.kpad;
+      if (v.s1) v.s1 += r0 * v.kpad;
+      if (v.s2) v.s2 += r0 * v.kpad;
+      if (v.s1h) v.s1h += r0 * v.kpad;
+      v.expo += r0;
+      return v;
+    };
+    for (int t = 0; t < np; ++t) {
+      const int64_t nt = ar.off[t + 1] - ar.off[t];
+      for (int s = 0; s <= t; ++s) {
+        const int64_t ns = ar.off[s + 1] - ar.off[s];
+        if (ns == 0 || nt == 0) continue;
+        {  // K_{ts} = (w/sqrt(pi)) sum_p w_p (x)_d A^(p)_{ts,d}, so that G = F_s K_{ts}^T = F_s K_{st}
+          ProfScope ps("build_K", st);
+          LRTEI_CUDA(launch_build_K(n, P, pl->d_C + (size_t)(t * np + s) * cblk, pl->d_w, pref, K, st));
+        }
+        {
+          ProfScope ps("split", st);
+          launch_split_rows(K, n3, n3, n3, Ksp, true, nslices(pl), st);
+        }
+        SplitMatrix Fs = rows_of(s), Ft = rows_of(t);
+        LRTEI_TRY(tc_gemm(Fs, Ksp, ns, n3, 1.0, G, n3, false, false, 1, nullptr, pl->d_status, st));
+        Gsp.rows = ns;
+        {
+          ProfScope ps("split", st);
+          launch_split_rows(G, ns, n3, n3, Gsp, false, nslices(pl), st);
+        }
+        LRTEI_TRY(tc_gemm(Gsp, Ft, ns, nt, 1.0, blk, nt, false, false, 1, nullptr, pl->d_status, st));
+        launch_scatter_block(blk, nt, ar.d_idx + ar.off[s], ns, ar.d_idx + ar.off[t], nt, Bu, npair, s != t, st);
+      }
+    }
+    return finish_launch("adaptive B (tensor cores)");
+  }
+  double *t1, *t2;
+  LRTEI_TRY(sc.get(&t1, (size_t)maxr * n3));
+  LRTEI_TRY(sc.get(&t2, (size_t)maxr * n3));
+  for (int t = 0; t < np; ++t) {
+    const int64_t nt = ar.off[t + 1] - ar.off[t];
+    for (int s = 0; s <= t; ++s) {
+      const int64_t ns = ar.off[s + 1] - ar.off[s];
+      if (ns == 0 || nt == 0) continue;
+      {  // rows of G = F_s K_{st}: K_{ts} applied to each row of F_s by mode products
+        ProfScope ps("kron", st);
+        launch_kron_apply(n, P, pl->d_C + (size_t)(t * np + s) * cblk, pl->d_w, ar.Fp + ar.off[s] * n3, G, ns, t1, t2,
+                          st);
+      }
+      {
+        ProfScope ps("gemm_fp64", st);
+        gemm_cuda_core<double>(false, true, ns, nt, n3, pref, G, n3, ar.Fp + ar.off[t] * n3, n3, 0.0, blk, nt, st);
+      }
+      launch_scatter_block(blk, nt, ar.d_idx + ar.off[s], ns, ar.d_idx + ar.off[t], nt, Bu, npair, s != t, st);
+    }
+  }
+  return finish_launch("adaptive B");
+}
+
+// J-build of an adaptive plan (FP64, every precision): X_t = F_t^T D_t per partition,
+// Y_s = sum_t K_{st} X_t (mode products with A_{st}), J_s = F_s Y_s.
+lrtei_status jbuild_adaptive(lrtei_plan* pl, const double* d_D, int R, double* d_J, cudaStream_t st) {
+  const int np = pl->npart, n = pl->n, P = pl->P, nbf = pl->basis.nbf;
+  const int64_t npair = pl->t.npair, n3 = (int64_t)n * n * n;
+  const size_t cblk = (size_t)3 * P * n * n;
+  const double pref = pl->omega / sqrt(kPi);
+  Scratch sc(st);
+  AdaptiveRows ar;
+  LRTEI_TRY(adaptive_rows(pl, sc, ar, true, st));
+  double *Du, *Dp, *X, *Yp, *Y, *t1, *t2, *Jp, *Ju;
+  LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&Dp, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&X, (size_t)np * R * n3));
+  LRTEI_TRY(sc.get(&Yp, (size_t)np * R * n3));
+  LRTEI_TRY(sc.get(&Y, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t1, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t2, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Jp, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&Ju, (size_t)npair * R));
+  launch_pack_density(nbf, R, d_D, Du, st);
+  launch_gather_rows(Du, ar.d_idx, npair, R, Dp, st);
+  for (int t = 0; t < np; ++t) {  // X_t^T (R x n^3) = D_t^T F_t
+    const int64_t nt = ar.off[t + 1] - ar.off[t];
+    ProfScope ps("gemm_fp64", st);
+    gemm_cuda_core<double>(true, false, R, n3, nt, 1.0, Dp + ar.off[t] * R, R, ar.Fp + ar.off[t] * n3, n3, 0.0,
+                           X + (size_t)t * R * n3, n3, st);
+  }
+  for (int s = 0; s < np; ++s) {
+    const int64_t ns = ar.off[s + 1] - ar.off[s];
+    for (int t = 0; t < np; ++t) {  // K_{st} X_t, rows of X_t^T: A_{st} by mode products
+      ProfScope ps("kron", st);
+      launch_kron_apply(n, P, pl->d_C + (size_t)(s * np + t) * cblk, pl->d_w, X + (size_t)t * R * n3,
+                        Yp + (size_t)t * R * n3, R, t1, t2, st);
+    }
+    launch_reduce_splits(Yp, np, (int64_t)R * n3, R, n3, n3, Y, n3, st);
+    {
+      ProfScope ps("gemm_fp64", st);
+      gemm_cuda_core<double>(false, true, ns, R, n3, pref, ar.Fp + ar.off[s] * n3, n3, Y, n3, 0.0, Jp + ar.off[s] * R,
+                             R, st);
+    }
+  }
+  launch_scatter_rows(Jp, ar.d_idx, npair, R, Ju, st);
+  launch_unpack_J(nbf, R, Ju, 1.0, d_J, pl->d_status, st);
+  return finish_launch("adaptive J-build");
+}
+
 int choose_form(const lrtei_plan* pl, lrtei_form form) {
   if (is_split(pl)) return LRTEI_FORM_FACTORED;  // the tensor-core path runs the factored form
   if (form == LRTEI_FORM_HADAMARD || form == LRTEI_FORM_FACTORED) return form;
@@ -994,6 +1278,7 @@ lrtei_status lrtei_assemble_Bu_rows(lrtei_plan* plan, lrtei_form form, int64_t r
     return LRTEI_ERR_ARG;
   }
   if (ld < plan->t.npair) { set_error("ld %lld < npair %lld", (long long)ld, (long long)plan->t.npair); return LRTEI_ERR_ARG; }
+  if (plan->npart > 0) { set_error("row ranges of B_u are not available for adaptive-box plans"); return LRTEI_ERR_UNSUPPORTED; }
   const int f = choose_form(plan, form);
   plan->last_form = f;
   return bu_rows(plan, f, row_begin, row_end, d_Bu, ld, (cudaStream_t)stream);
@@ -1029,6 +1314,22 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
   cudaStream_t st = (cudaStream_t)stream;
   const int f = choose_form(plan, form);
   plan->last_form = f;
+  if (plan->npart > 0) {  // adaptive boxes: partition blocks of the factored form
+    plan->last_form = LRTEI_FORM_FACTORED;
+    if (hB && d_B == nullptr) {
+      set_error("adaptive plans write B through the device alias of pinned host memory (map it)");
+      return LRTEI_ERR_ARG;
+    }
+    Scratch sc(st);
+    double* Bu;
+    LRTEI_TRY(sc.get(&Bu, (size_t)npair * npair));
+    LRTEI_TRY(bu_adaptive(plan, Bu, st));
+    {
+      ProfScope ps("expand_B", st);
+      launch_expand_B(plan->t, nbf, Bu, npair, 1.0, d_B, ld, plan->d_status, st);
+    }
+    return finish_launch("expand_B");
+  }
   if (hB && is_split(plan)) return assemble_B_host_banded(plan, hB, ld, st);
   // process B_u in row blocks of at most ~1 GiB
   int64_t rb = std::max<int64_t>(1, (int64_t)((1ULL << 30) / (sizeof(double) * (size_t)npair)));
@@ -1062,12 +1363,17 @@ lrtei_status lrtei_entries(lrtei_plan* plan, const int32_t* d_idx4, int64_t coun
   if (count < 0 || (count > 0 && (!d_idx4 || !d_out))) { set_error("invalid entries arguments"); return LRTEI_ERR_ARG; }
   if (count == 0) return LRTEI_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  LRTEI_TRY(ensure_T(plan, st));
+  if (plan->npart == 0) LRTEI_TRY(ensure_T(plan, st));
   Scratch sc(st);
   int64_t *r, *c;
   LRTEI_TRY(sc.get(&r, count));
   LRTEI_TRY(sc.get(&c, count));
   launch_idx4_to_pairs(plan->basis.nbf, d_idx4, count, r, c, plan->d_status, st);
+  if (plan->npart > 0) {
+    launch_adaptive_entries(plan->t, plan->n, plan->P, plan->npart, plan->d_pair_part, plan->d_S, plan->d_C,
+                            plan->d_w, plan->omega / sqrt(kPi), r, c, count, d_out, plan->d_status, st);
+    return finish_launch("entries (adaptive)");
+  }
   launch_hadamard_pairs(plan->t, plan->n, plan->P, plan->d_S, plan->d_T, plan->d_w, plan->omega / sqrt(kPi), r, c,
                         count, d_out, plan->d_status, st);
   return finish_launch("entries");
@@ -1079,7 +1385,8 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = plan->n, P = plan->P, nrows = plan->t.nrows;
   if (d_S) LRTEI_CUDA(cudaMemcpyAsync(d_S, plan->d_S, sizeof(double) * 3 * nrows * n, cudaMemcpyDeviceToDevice, st));
-  if (d_C) LRTEI_CUDA(cudaMemcpyAsync(d_C, plan->d_C, sizeof(double) * 3 * P * n * n, cudaMemcpyDeviceToDevice, st));
+  const size_t nb2c = (size_t)std::max(1, plan->npart) * std::max(1, plan->npart);  // coefficient blocks
+  if (d_C) LRTEI_CUDA(cudaMemcpyAsync(d_C, plan->d_C, sizeof(double) * nb2c * 3 * P * n * n, cudaMemcpyDeviceToDevice, st));
   if (d_s) LRTEI_CUDA(cudaMemcpyAsync(d_s, plan->d_s, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
   if (d_w) LRTEI_CUDA(cudaMemcpyAsync(d_w, plan->d_w, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
   if (d_c) LRTEI_CUDA(cudaMemcpyAsync(d_c, plan->t.row_c, sizeof(double) * nrows, cudaMemcpyDeviceToDevice, st));
@@ -1088,12 +1395,121 @@ lrtei_status lrtei_factors(lrtei_plan* plan, double* d_S, double* d_C, double* d
 
 lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream) {
   if (!plan || !d_K) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (plan->npart > 0) { set_error("adaptive-box plans have one K per partition pair"); return LRTEI_ERR_UNSUPPORTED; }
   {
     ProfScope ps("build_K", (cudaStream_t)stream);
     LRTEI_CUDA(launch_build_K(plan->n, plan->P, plan->d_C, plan->d_w, plan->omega / sqrt(kPi), d_K,
                               (cudaStream_t)stream));
   }
   return finish_launch("dense K");
+}
+
+// Long-range exchange (appendix, eq. exchange) through the factored form, in blocks of orbitals:
+// X = Q_b MT^T (N_b n^3 columns per orbital), Y = X K, K^lr += 2 Yp Xp^T with the orbital index
+// moved into the contraction (Xp[mu][(j, m)]).  Tensor-core precisions run the three products on
+// tcgen05 (split operands); FP64 / FP32 plans run them on the CUDA cores in FP64, with K applied by
+// mode products (eq. ig1).
+lrtei_status lrtei_exchange(lrtei_plan* plan, const double* d_Q, int norb, double* d_K, void* stream) {
+  if (!plan || !d_Q || !d_K) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
+  if (norb <= 0) { set_error("norb must be positive (got %d)", norb); return LRTEI_ERR_ARG; }
+  if (plan->npart > 0) { set_error("the exchange of adaptive-box plans is not supported"); return LRTEI_ERR_UNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nbf = plan->basis.nbf, n = plan->n, P = plan->P;
+  const int64_t n3 = (int64_t)n * n * n, rowlen = (int64_t)nbf * n3;
+  const double pref = plan->omega / sqrt(kPi);
+  const bool tc = is_split(plan);
+  ProfScope ps_all("exchange", st);
+  LRTEI_TRY(ensure_F64(plan, st));
+  // orbital block: the block's X (ob N_b x n^3, FP64) within ~1 GiB
+  int ob = (int)std::max<int64_t>(1, std::min<int64_t>(norb, (int64_t)((1ULL << 30) / (sizeof(double) * rowlen))));
+  if (env_count("LRTEI_EXCHANGE_BLOCK") > 0) ob = (int)std::min<int64_t>(norb, env_count("LRTEI_EXCHANGE_BLOCK"));
+  const int nblk = (norb + ob - 1) / ob;
+  Scratch sc(st);
+  double *MT, *X, *Y, *Xp, *Yp, *Kb;
+  LRTEI_TRY(sc.get(&MT, (size_t)rowlen * nbf));
+  LRTEI_TRY(sc.get(&X, (size_t)ob * rowlen));
+  LRTEI_TRY(sc.get(&Y, (size_t)ob * rowlen));
+  LRTEI_TRY(sc.get(&Xp, (size_t)ob * rowlen));
+  LRTEI_TRY(sc.get(&Yp, (size_t)ob * rowlen));
+  LRTEI_TRY(sc.get(&Kb, (size_t)nblk * nbf * nbf));
+  launch_gather_MT(nbf, n3, plan->d_F, n3, MT, st);
+  if (tc) {
+    LRTEI_TRY(ensure_Ksp(plan, st, true));  // K as the B operand of Y = X K^T (K symmetric)
+    SplitMatrix Qsp, MTsp, Xsp, Ypsp, Xpsp;
+    LRTEI_TRY(scratch_split(sc, Qsp, norb, nbf, false, plan));
+    LRTEI_TRY(scratch_split(sc, MTsp, rowlen, nbf, true, plan));
+    LRTEI_TRY(scratch_split(sc, Xsp, (int64_t)ob * nbf, n3, false, plan));
+    LRTEI_TRY(scratch_split(sc, Ypsp, nbf, (int64_t)ob * n3, false, plan));
+    LRTEI_TRY(scratch_split(sc, Xpsp, nbf, (int64_t)ob * n3, true, plan));
+    const int sK = splits_for(nbf, (int64_t)ob * n3);
+    double* part;
+    LRTEI_TRY(sc.get(&part, (size_t)sK * nbf * nbf));
+    {
+      ProfScope ps("split", st);
+      launch_split_rows(d_Q, norb, nbf, nbf, Qsp, false, nslices(plan), st);
+      launch_split_rows(MT, rowlen, nbf, nbf, MTsp, true, nslices(plan), st);
+    }
+    for (int b = 0; b < nblk; ++b) {
+      const int j0 = b * ob, nj = std::min(ob, norb - j0);
+      SplitMatrix Qb = Qsp;  // rows [j0, j0 + nj)
+      Qb.rows = nj;
+      Qb.s0 += (int64_t)j0 * Qb.kpad;
+      if (Qb.s1) Qb.s1 += (int64_t)j0 * Qb.kpad;
+      if (Qb.s2) Qb.s2 += (int64_t)j0 * Qb.kpad;
+      if (Qb.s1h) Qb.s1h += (int64_t)j0 * Qb.kpad;
+      Qb.expo += j0;
+      LRTEI_TRY(tc_gemm(Qb, MTsp, nj, rowlen, 1.0, X, rowlen, false, false, 1, nullptr, plan->d_status, st));
+      SplitMatrix Xb = Xsp;
+      Xb.rows = (int64_t)nj * nbf;
+      {
+        ProfScope ps("split", st);
+        launch_split_rows(X, Xb.rows, n3, n3, Xb, false, nslices(plan), st);
+      }
+      LRTEI_TRY(tc_gemm(Xb, plan->Ksp, Xb.rows, n3, 1.0, Y, n3, false, false, 1, nullptr, plan->d_status, st));
+      launch_perm_orbital_rows(nbf, n3, nj, X, Xp, st);
+      launch_perm_orbital_rows(nbf, n3, nj, Y, Yp, st);
+      SplitMatrix Ya = Ypsp, Xa = Xpsp;
+      Ya.kpad = Xa.kpad = kpad256((int64_t)nj * n3);
+      {
+        ProfScope ps("split", st);
+        launch_split_rows(Yp, nbf, (int64_t)nj * n3, (int64_t)nj * n3, Ya, false, nslices(plan), st);
+        launch_split_rows(Xp, nbf, (int64_t)nj * n3, (int64_t)nj * n3, Xa, true, nslices(plan), st);
+      }
+      LRTEI_TRY(tc_gemm(Ya, Xa, nbf, nbf, 2.0, Kb + (size_t)b * nbf * nbf, nbf, false, false,
+                        splits_for(nbf, (int64_t)nj * n3), part, plan->d_status, st));
+    }
+  } else {
+    double *t1, *t2;
+    LRTEI_TRY(sc.get(&t1, (size_t)ob * rowlen));
+    LRTEI_TRY(sc.get(&t2, (size_t)ob * rowlen));
+    const int64_t kc = 32768;  // split-K chunk of the last product (an N_b x N_b output)
+    const int64_t maxk = (int64_t)ob * n3, nchunk = (maxk + kc - 1) / kc;
+    double* part;
+    LRTEI_TRY(sc.get(&part, (size_t)nchunk * nbf * nbf));
+    for (int b = 0; b < nblk; ++b) {
+      const int j0 = b * ob, nj = std::min(ob, norb - j0);
+      {
+        ProfScope ps("gemm_fp64", st);
+        gemm_cuda_core<double>(false, true, nj, rowlen, nbf, 1.0, d_Q + (size_t)j0 * nbf, nbf, MT, nbf, 0.0, X, rowlen, st);
+      }
+      {
+        ProfScope ps("kron", st);
+        launch_kron_apply(n, P, plan->d_C, plan->d_w, X, Y, (int64_t)nj * nbf, t1, t2, st);
+      }
+      launch_perm_orbital_rows(nbf, n3, nj, X, Xp, st);
+      launch_perm_orbital_rows(nbf, n3, nj, Y, Yp, st);
+      const int64_t K = (int64_t)nj * n3, nc = (K + kc - 1) / kc;
+      for (int64_t q = 0; q < nc; ++q) {
+        const int64_t k0 = q * kc, kk = std::min(kc, K - k0);
+        ProfScope ps("gemm_fp64", st);
+        gemm_cuda_core<double>(false, true, nbf, nbf, kk, 2.0 * pref, Yp + k0, K, Xp + k0, K, 0.0,
+                               part + (size_t)q * nbf * nbf, nbf, st);
+      }
+      launch_reduce_splits(part, (int)nc, (int64_t)nbf * nbf, nbf, nbf, nbf, Kb + (size_t)b * nbf * nbf, nbf, st);
+    }
+  }
+  launch_reduce_splits(Kb, nblk, (int64_t)nbf * nbf, nbf, nbf, nbf, d_K, nbf, st);
+  return finish_launch("exchange");
 }
 
 // Khatri-Rao low-rank compression (Section 6, eq. SVD and eq. approxepsilon): S_d -> S_d V_d and
@@ -1108,6 +1524,7 @@ lrtei_status lrtei_plan_compress(lrtei_plan* plan, double eps, int max_rank, dou
     return LRTEI_ERR_ARG;
   }
   if (plan->kr_rank > 0) { set_error("the plan is already compressed (rank %d)", plan->kr_rank); return LRTEI_ERR_UNSUPPORTED; }
+  if (plan->npart > 0) { set_error("compression of adaptive-box plans is not supported"); return LRTEI_ERR_UNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
   const int n = plan->n, P = plan->P;
   const int64_t nrows = plan->t.nrows;
@@ -1345,6 +1762,7 @@ static int64_t jbuild_stream_block(const lrtei_plan* plan) {
 // One J-build launched kernel by kernel (also what a captured graph replays).
 static lrtei_status jbuild_direct(lrtei_plan* plan, const double* d_D, int R, double* d_J, cudaStream_t st) {
   ProfScope ps_all("jbuild", st);
+  if (plan->npart > 0) return jbuild_adaptive(plan, d_D, R, d_J, st);
   const int64_t rb = jbuild_stream_block(plan);
   if (rb > 0) return jbuild_streamed(plan, d_D, R, d_J, rb, st);
   if (is_split(plan)) return jbuild_tc(plan, d_D, R, d_J, st);
@@ -1387,6 +1805,7 @@ lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_
   if (!plan || !d_D || !d_J) { set_error("NULL argument"); return LRTEI_ERR_ARG; }
   if (R <= 0) { set_error("R must be positive (got %d)", R); return LRTEI_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
+  if (plan->npart > 0) return jbuild_direct(plan, d_D, R, d_J, st);
   const char* g = getenv("LRTEI_JBUILD_GRAPH");
   const bool graphs = !(g && g[0] == '0');
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1405,6 +1824,10 @@ lrtei_status lrtei_jbuild_batched(lrtei_plan* const* plans, int nmol, const doub
     if (!plans[m] || !d_D[m] || !d_J[m] || R[m] <= 0) {
       set_error("batched J-build: molecule %d has a NULL plan/pointer or R <= 0", m);
       return LRTEI_ERR_ARG;
+    }
+    if (plans[m]->npart > 0) {
+      set_error("batched J-build: molecule %d has an adaptive-box plan (use lrtei_jbuild)", m);
+      return LRTEI_ERR_UNSUPPORTED;
     }
     if (is_split(plans[m]) != is_split(plans[0])) {
       set_error("batched J-build: all plans must use tensor-core or all CUDA-core precision");
@@ -1433,6 +1856,7 @@ lrtei_status plan_view(const lrtei_plan* plan, PlanView* v) {
   v->status = plan->d_status;
   v->half3 = plan->d_half3;
   v->kr_rank = plan->kr_rank;
+  v->npart = plan->npart;
   return LRTEI_OK;
 }
 }  // namespace lrtei

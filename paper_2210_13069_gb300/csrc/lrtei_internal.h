@@ -94,6 +94,10 @@ void launch_gauss_legendre(int N, double* d_z, double* d_w, cudaStream_t st);
 void launch_nodes_map(int P, double omega, const double* d_z, double* d_s, cudaStream_t st);
 // C[d][p] = Chebyshev coefficients of exp(-s_p^2 half_d^2 (u - v)^2), n x n.
 void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, double* d_C, cudaStream_t st);
+// The same between two intervals of half-widths hx3[d] (first index) and hy3[d] (second index),
+// both centred at the same point (the adaptive boxes of Section 6).
+void launch_cheb_coeff_cross(int n, int P, const double* d_s, const double* d_hx3, const double* d_hy3, double* d_C,
+                             cudaStream_t st);
 // Normalised coefficients per (basis function, primitive).
 void launch_normalise(int nbf, const int* d_bf_shell, const int* d_bf_pow, const int* d_shell_nprim,
                       const int* d_shell_poff, const double* d_exps, const double* d_coefs, const int* d_bf_coff,
@@ -104,9 +108,11 @@ void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf
                       const int* d_bf_coff, const double* d_ncoef, cudaStream_t st);
 // S[d][row][m] for m < n, FP64.  d_gz/d_gw: kMomentPts Gauss-Legendre rule on [-1,1].
 // Items (d, row) = rep[i] (d nrows + row; i < nitems; rep NULL: i itself, nitems = 3 nrows; rep[i] < 0:
-// skipped) -> d_S[i][m].
-void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const double* d_gz,
-                    const double* d_gw, const int64_t* d_rep, int64_t nitems, double* d_S, cudaStream_t st);
+// skipped) -> d_S[i][m].  The box of a row is [lo3[3 b + d], hi3[3 b + d]] with b = row_box[row]
+// (row_box NULL: b = 0).
+void launch_moments(const PairTable& t, int n, const double* d_lo3, const double* d_hi3, const uint8_t* d_row_box,
+                    const double* d_gz, const double* d_gw, const int64_t* d_rep, int64_t nitems, double* d_S,
+                    cudaStream_t st);
 // Moment keys: rows that share shell pair, primitive pair, d and the powers in d share S_d.
 // key[d nrows + row] in [0, nkeys) with nkeys = sum over shell pairs s1 <= s2 of
 // K_s1 K_s2 3 (l_s1 + 1)(l_s2 + 1) (offsets sp_off, triangular in the shell pair); rep[key] = one
@@ -171,6 +177,27 @@ cudaError_t launch_kr_svd(int64_t nrows, int n, const double* d_S, double* d_par
 cudaError_t launch_kr_project(int64_t nrows, int n, int P, int R, const double* d_S, const double* d_C,
                               const double* d_V, double* d_Snew, double* d_Cnew, cudaStream_t st);
 
+// ---------------------------------------------------------------- adaptive boxes (Section 6)
+// out[i][:] = in[idx[i]][:] (rows of length len, both with leading dimension len).
+void launch_gather_rows(const double* d_in, const int64_t* d_idx, int64_t count, int64_t len, double* d_out,
+                        cudaStream_t st);
+// Bu[rows[i]][cols[j]] = blk[i][j] (ldb), and Bu[cols[j]][rows[i]] too when mirror.
+void launch_scatter_block(const double* d_blk, int64_t ldb, const int64_t* d_rows, int64_t nr, const int64_t* d_cols,
+                          int64_t nc, double* d_Bu, int64_t ldu, bool mirror, cudaStream_t st);
+// Ju[rows[i]][:] = blk[i][:] (R columns).
+void launch_scatter_rows(const double* d_blk, const int64_t* d_rows, int64_t nr, int64_t R, double* d_Ju,
+                         cudaStream_t st);
+// Algorithm 1 entries with per-pair partitions: C block (part[r], part[c]) of Cpp (npart^2 x 3 x P x n x n).
+void launch_adaptive_entries(const PairTable& t, int n, int P, int npart, const int* d_pair_part, const double* d_S,
+                             const double* d_Cpp, const double* d_w, double pref, const int64_t* d_r,
+                             const int64_t* d_c, int64_t count, double* d_out, int* d_status, cudaStream_t st);
+
+// ---------------------------------------------------------------- long-range exchange
+// MT[(mu n3 + m) nbf + la] = F[pair(mu, la) ldF + m]  (nbf n3 rows of nbf).
+void launch_gather_MT(int nbf, int64_t n3, const double* d_F, int64_t ldF, double* d_MT, cudaStream_t st);
+// Zp[mu][j n3 + m] = Z[(j nbf + mu) n3 + m] for j < nj.
+void launch_perm_orbital_rows(int nbf, int64_t n3, int nj, const double* d_Z, double* d_Zp, cudaStream_t st);
+
 // ---------------------------------------------------------------- CUDA-core GEMM
 // C[M x N] = alpha * op(A) op(B) + beta * C, row-major; transA: A is K x M; transB: B is N x K.
 template <typename T>
@@ -227,6 +254,7 @@ struct PlanView {
   int* status;      // the plan's device status word
   const double* half3;  // box half-widths per dimension (device)
   int kr_rank;      // 0, or the rank of a Khatri-Rao compressed plan
+  int npart;        // 0, or the number of adaptive-box partitions
 };
 lrtei_status plan_view(const lrtei_plan* plan, PlanView* v);
 

@@ -128,6 +128,10 @@ extern "C" lrtei_status lrtei_entries_noalloc(lrtei_plan* plan, const int32_t* d
     set_error("invalid entries arguments");
     return LRTEI_ERR_ARG;
   }
+  if (v.npart > 0) {  // one coefficient block per partition pair: lrtei_entries handles these plans
+    set_error("lrtei_entries_noalloc: adaptive-box plans are not supported");
+    return LRTEI_ERR_UNSUPPORTED;
+  }
   if (count > kNoAllocMaxEntries) {
     set_error("lrtei_entries_noalloc: %lld entries requested, at most %lld per call (fixed scratch of %lld bytes)",
               (long long)count, (long long)kNoAllocMaxEntries, (long long)(2 * kNoAllocMaxEntries * sizeof(int64_t)));

@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
                 ("P", ctypes.c_int), ("omega", ctypes.c_double), ("box_lo", ctypes.c_double * 3),
                 ("box_hi", ctypes.c_double * 3), ("precision", ctypes.c_int), ("last_form", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_size_t), ("tau_screening", ctypes.c_double), ("cheb_n", ctypes.c_int),
-                ("kr_rank", ctypes.c_int)]
+                ("kr_rank", ctypes.c_int), ("npartitions", ctypes.c_int), ("partition_b", ctypes.c_double * 8)]
 
 
 _lib = None
@@ -68,6 +68,8 @@ def load():
                                   ctypes.POINTER(VP)]),
         "lrtei_plan_create_ex": (S, [VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, DP, DP, ctypes.c_int,
                                      ctypes.c_double, VP, ctypes.POINTER(VP)]),
+        "lrtei_plan_create_adaptive": (S, [VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, VP, ctypes.POINTER(VP)]),
         "lrtei_plan_destroy": (None, [VP]),
         "lrtei_plan_info_get": (S, [VP, ctypes.POINTER(PlanInfo)]),
         "lrtei_plan_status": (S, [VP]),
@@ -80,6 +82,7 @@ def load():
         "lrtei_dense_K": (S, [VP, VP, VP]),
         "lrtei_plan_compress": (S, [VP, ctypes.c_double, ctypes.c_int, DP, IP, VP]),
         "lrtei_jbuild": (S, [VP, VP, ctypes.c_int, VP, VP]),
+        "lrtei_exchange": (S, [VP, VP, ctypes.c_int, VP, VP]),
         "lrtei_jbuild_batched": (S, [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(VP), IP, ctypes.POINTER(VP),
                                      VP]),
         "lrtei_selector_create": (S, [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(VP)]),
@@ -188,6 +191,14 @@ def lrtei_plan_create_ex(basis: int, omega: float, n: int, P: int, box_lo=None, 
     return out.value
 
 
+def lrtei_plan_create_adaptive(basis: int, omega: float, n: int, P: int, tau_adaptive: float, npartitions: int,
+                               precision: int = LRTEI_FP64, stream=None) -> int:
+    out = VP()
+    _check(load().lrtei_plan_create_adaptive(basis, float(omega), int(n), int(P), float(tau_adaptive),
+                                             int(npartitions), int(precision), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
 def lrtei_plan_destroy(plan: int):
     load().lrtei_plan_destroy(plan)
 
@@ -198,7 +209,8 @@ def lrtei_plan_info_get(plan: int) -> dict:
     return {"nbf": info.nbf, "npair": info.npair, "nrows": info.nrows, "n": info.n, "P": info.P,
             "omega": info.omega, "box_lo": list(info.box_lo), "box_hi": list(info.box_hi),
             "precision": info.precision, "last_form": info.last_form, "workspace_bytes": info.workspace_bytes,
-            "tau_screening": info.tau_screening, "cheb_n": info.cheb_n, "kr_rank": info.kr_rank}
+            "tau_screening": info.tau_screening, "cheb_n": info.cheb_n, "kr_rank": info.kr_rank,
+            "npartitions": info.npartitions, "partition_b": list(info.partition_b)[:info.npartitions]}
 
 
 def lrtei_plan_status(plan: int):
@@ -253,6 +265,10 @@ def lrtei_dense_K(plan: int, d_K, stream=None):
 
 def lrtei_jbuild(plan: int, d_D, R: int, d_J, stream=None):
     _check(load().lrtei_jbuild(plan, _ptr(d_D), int(R), _ptr(d_J), _stream(stream)))
+
+
+def lrtei_exchange(plan: int, d_Q, norb: int, d_K, stream=None):
+    _check(load().lrtei_exchange(plan, _ptr(d_Q), int(norb), _ptr(d_K), _stream(stream)))
 
 
 def lrtei_jbuild_batched(plans: Sequence[int], d_D: Sequence, R: Sequence[int], d_J: Sequence, stream=None):
@@ -391,12 +407,17 @@ class Plan:
     """A basis plus a plan on the current CUDA device (owns both handles)."""
 
     def __init__(self, mol, precision: str = "fp64", stream=None, n=None, P=None, omega=None,
-                 tau_screening: float = 0.0):
+                 tau_screening: float = 0.0, adaptive=None):
+        """adaptive=(tau_adaptive, npartitions) creates an adaptive-box plan (no explicit box)."""
         import torch
         centers, ls, nprim, exps, coefs = mol.packed()
         self.basis = lrtei_basis_create(centers, ls, nprim, exps, coefs)
-        self.plan = lrtei_plan_create_ex(self.basis, omega or mol.omega, n or mol.n, P or mol.P, mol.box_lo,
-                                         mol.box_hi, PRECISIONS[precision], tau_screening, stream)
+        if adaptive is not None:
+            self.plan = lrtei_plan_create_adaptive(self.basis, omega or mol.omega, n or mol.n, P or mol.P,
+                                                   adaptive[0], adaptive[1], PRECISIONS[precision], stream)
+        else:
+            self.plan = lrtei_plan_create_ex(self.basis, omega or mol.omega, n or mol.n, P or mol.P, mol.box_lo,
+                                             mol.box_hi, PRECISIONS[precision], tau_screening, stream)
         self.info = lrtei_plan_info_get(self.plan)
         self.nbf = self.info["nbf"]
         self.npair = self.info["npair"]
@@ -472,6 +493,15 @@ class Plan:
         sig, ranks = lrtei_plan_compress(self.plan, eps, max_rank, self.info["n"], stream)
         self.info = lrtei_plan_info_get(self.plan)
         return sig, ranks
+
+    def exchange(self, Q, out=None, stream=None):
+        """K^lr (N_b x N_b) for orbital coefficients Q (norb x N_b), eq. exchange."""
+        torch = self._torch
+        Q = Q.contiguous()
+        if out is None:
+            out = torch.empty((self.nbf, self.nbf), dtype=torch.float64, device="cuda")
+        lrtei_exchange(self.plan, Q, Q.shape[0], out, stream)
+        return out
 
     def status(self):
         lrtei_plan_status(self.plan)
