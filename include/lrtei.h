@@ -242,6 +242,25 @@ lrtei_status lrtei_dense_K(lrtei_plan* plan, double* d_K, void* stream);
  * keeps the choices of the call it was captured from. */
 lrtei_status lrtei_jbuild(lrtei_plan* plan, const double* d_D, int R, double* d_J, void* stream);
 
+/* ---- a J-build split over ranks by unique pairs -----------------------------------------
+ * The two halves of eq. coulapprox for one range [pair_begin, pair_end) of unique pairs (rows of
+ * F_u, pair order as in lrtei_assemble_Bu_rows), for callers that shard a molecule's J-builds over
+ * processes or GPUs:
+ *   lrtei_jbuild_partial_x: d_X (device, R x n^3, FP64) = sum over the range of u_r F_u(r, :), where
+ *     u_r = D(mu, nu) (mu == nu) or 2 D(mu, nu) are the densities d_D (as lrtei_jbuild) on pair r;
+ *     the sum of the ranks' d_X over a partition of [0, npair) is X = F_u^T vec(D) (an all-reduce).
+ *   lrtei_jbuild_apply_x: from the summed d_X, Y = sum_p w_p (A_x^p (x) A_y^p (x) A_z^p) X by mode
+ *     products (eq. ig1, FP64), then J(mu, nu) = J(nu, mu) = (w/sqrt(pi)) F_u(r, :) Y for the pairs
+ *     r of the range; every other entry of d_J (R x N_b x N_b) is set to 0, so the sum of the
+ *     ranks' d_J is lrtei_jbuild's J (a second all-reduce).
+ * Rows of F_u are built for the range on each call (FP64); split precisions contract them on the
+ * tensor cores.  LRTEI_ERR_ARG for a range outside [0, npair); adaptive-box plans return
+ * LRTEI_ERR_UNSUPPORTED. */
+lrtei_status lrtei_jbuild_partial_x(lrtei_plan* plan, const double* d_D, int R, int64_t pair_begin, int64_t pair_end,
+                                    double* d_X, void* stream);
+lrtei_status lrtei_jbuild_apply_x(lrtei_plan* plan, const double* d_X, int R, int64_t pair_begin, int64_t pair_end,
+                                  double* d_J, void* stream);
+
 /* ---- long-range exchange (appendix "The Hartree-Fock exchange", eq. exchange) -------------
  * K^lr(mu, nu) = 2 sum_j sum_{la, ka} q_{j la} q_{j ka} B(mu la, ka nu) for the orbital
  * coefficients d_Q (device, norb x N_b, row-major) into d_K (device, N_b x N_b, row-major),

@@ -345,6 +345,35 @@ void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStr
   k_pack_density<<<(unsigned)blocks, 256, 0, st>>>(nbf, R, npair, d_D, d_u);
 }
 
+// J_q(mu, nu) = J_q(nu, mu) = scale * Ju[r - r0][q] for the unique pairs r in [r0, r1); J is
+// zeroed first by the caller.  One thread per (r, q).
+__global__ void k_unpack_J_range(int nbf, int R, int64_t r0, int64_t r1, const int* __restrict__ pair_mu,
+                                 const int* __restrict__ pair_nu, const double* __restrict__ Ju, double scale,
+                                 double* __restrict__ J, int* status) {
+  const int64_t total = (r1 - r0) * R;
+  bool bad = false;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = r0 + t / R;
+    const int q = (int)(t % R);
+    const int mu = pair_mu[r], nu = pair_nu[r];
+    const double v = scale * Ju[t];
+    bad |= !isfinite(v);
+    J[(size_t)q * nbf * nbf + (size_t)mu * nbf + nu] = v;
+    J[(size_t)q * nbf * nbf + (size_t)nu * nbf + mu] = v;
+  }
+  latch_nonfinite_warp(status, bad);
+}
+
+void launch_unpack_J_range(const PairTable& t, int nbf, int R, int64_t r0, int64_t r1, const double* d_Ju, double scale,
+                           double* d_J, int* d_status, cudaStream_t st) {
+  if (r1 <= r0) return;
+  const int64_t total = (r1 - r0) * R;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch();
+  k_unpack_J_range<<<(unsigned)blocks, 256, 0, st>>>(nbf, R, r0, r1, t.pair_mu, t.pair_nu, d_Ju, scale, d_J, d_status);
+}
+
 // J_q(mu, nu) = J_q(nu, mu) = scale * Ju[r][q].
 __global__ void k_unpack_J(int nbf, int R, const double* __restrict__ Ju, double scale, double* __restrict__ J,
                            int* status) {

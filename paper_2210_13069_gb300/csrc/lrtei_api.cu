@@ -1733,6 +1733,106 @@ static lrtei_status jbuild_streamed(lrtei_plan* plan, const double* d_D, int R, 
   return finish_launch("jbuild (streamed, tensor cores)");
 }
 
+// ---- a J-build split over ranks by unique pairs (the two halves of eq. coulapprox) -------------
+// X^T (R x n^3) = sum over the pairs r in [r0, r1) of u_r F_u(r, :), u the packed densities; the
+// ranks' X are summed (an all-reduce) and each rank then forms its rows of J_u = F_u Y from the
+// node sum Y = K X.  F_u rows of the range are built here (FP64) and contracted on the tensor cores
+// (split plans) or the CUDA cores.
+static lrtei_status check_range(const lrtei_plan* plan, int64_t r0, int64_t r1) {
+  if (r0 < 0 || r1 > plan->t.npair || r0 > r1) {
+    set_error("pair range [%lld, %lld) outside [0, %lld)", (long long)r0, (long long)r1, (long long)plan->t.npair);
+    return LRTEI_ERR_ARG;
+  }
+  if (plan->npart > 0) { set_error("pair ranges of adaptive-box plans are not supported"); return LRTEI_ERR_UNSUPPORTED; }
+  return LRTEI_OK;
+}
+
+lrtei_status lrtei_jbuild_partial_x(lrtei_plan* plan, const double* d_D, int R, int64_t pair_begin, int64_t pair_end,
+                                    double* d_X, void* stream) {
+  if (!plan || !d_D || !d_X || R <= 0) { set_error("invalid partial J-build arguments"); return LRTEI_ERR_ARG; }
+  LRTEI_TRY(check_range(plan, pair_begin, pair_end));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nbf = plan->basis.nbf, n = plan->n;
+  const int64_t npair = plan->t.npair, n3 = (int64_t)n * n * n, nr = pair_end - pair_begin;
+  if (nr == 0) {
+    LRTEI_CUDA(cudaMemsetAsync(d_X, 0, sizeof(double) * (size_t)R * n3, st));
+    return LRTEI_OK;
+  }
+  ProfScope ps_all("jbuild", st);
+  Scratch sc(st);
+  double *Du, *Fb;
+  LRTEI_TRY(sc.get(&Du, (size_t)npair * R));
+  LRTEI_TRY(sc.get(&Fb, (size_t)nr * n3));
+  launch_pack_density(nbf, R, d_D, Du, st);
+  launch_build_F<double>(plan->t, n, plan->d_S, pair_begin, pair_end, Fb, n3, st);
+  if (!is_split(plan)) {
+    ProfScope ps("gemm_fp64", st);
+    gemm_cuda_core<double>(true, false, R, n3, nr, 1.0, Du + pair_begin * R, R, Fb, n3, 0.0, d_X, n3, st);
+    return finish_launch("partial X");
+  }
+  double *FbT, *DbT, *part;
+  LRTEI_TRY(sc.get(&FbT, (size_t)nr * n3));
+  LRTEI_TRY(sc.get(&DbT, (size_t)R * nr));
+  const int sb = splits_for(n3, nr);
+  LRTEI_TRY(sc.get(&part, (size_t)sb * n3 * R));
+  SplitMatrix A, Bm;
+  LRTEI_TRY(scratch_split(sc, A, n3, nr, false, plan));
+  LRTEI_TRY(scratch_split(sc, Bm, R, nr, true, plan));
+  launch_transpose(Fb, nr, n3, n3, FbT, nr, st);
+  launch_transpose(Du + pair_begin * R, nr, R, R, DbT, nr, st);
+  {
+    ProfScope ps("split", st);
+    launch_split_rows(FbT, n3, nr, nr, A, false, nslices(plan), st);
+    launch_split_rows(DbT, R, nr, nr, Bm, true, nslices(plan), st);
+  }
+  LRTEI_TRY(tc_gemm(A, Bm, n3, R, 1.0, d_X, n3, true, false, sb, part, plan->d_status, st));
+  return finish_launch("partial X (tensor cores)");
+}
+
+lrtei_status lrtei_jbuild_apply_x(lrtei_plan* plan, const double* d_X, int R, int64_t pair_begin, int64_t pair_end,
+                                  double* d_J, void* stream) {
+  if (!plan || !d_X || !d_J || R <= 0) { set_error("invalid partial J-build arguments"); return LRTEI_ERR_ARG; }
+  LRTEI_TRY(check_range(plan, pair_begin, pair_end));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nbf = plan->basis.nbf, n = plan->n, P = plan->P;
+  const int64_t n3 = (int64_t)n * n * n, nr = pair_end - pair_begin;
+  const double pref = plan->omega / sqrt(kPi);
+  LRTEI_CUDA(cudaMemsetAsync(d_J, 0, sizeof(double) * (size_t)R * nbf * nbf, st));
+  if (nr == 0) return LRTEI_OK;
+  ProfScope ps_all("jbuild", st);
+  Scratch sc(st);
+  double *Y, *t1, *t2, *Fb, *Ju;
+  LRTEI_TRY(sc.get(&Y, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t1, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&t2, (size_t)R * n3));
+  LRTEI_TRY(sc.get(&Fb, (size_t)nr * n3));
+  LRTEI_TRY(sc.get(&Ju, (size_t)nr * R));
+  {
+    ProfScope ps("kron", st);
+    launch_kron_apply(n, P, plan->d_C, plan->d_w, d_X, Y, R, t1, t2, st);
+  }
+  launch_build_F<double>(plan->t, n, plan->d_S, pair_begin, pair_end, Fb, n3, st);
+  if (!is_split(plan)) {
+    ProfScope ps("gemm_fp64", st);
+    gemm_cuda_core<double>(false, true, nr, R, n3, 1.0, Fb, n3, Y, n3, 0.0, Ju, R, st);
+  } else {
+    double* part;
+    const int s3 = splits_for(nr, n3);
+    LRTEI_TRY(sc.get(&part, (size_t)s3 * nr * R));
+    SplitMatrix A, Ysp;
+    LRTEI_TRY(scratch_split(sc, A, nr, n3, false, plan));
+    LRTEI_TRY(scratch_split(sc, Ysp, R, n3, true, plan));
+    {
+      ProfScope ps("split", st);
+      launch_split_rows(Fb, nr, n3, n3, A, false, nslices(plan), st);
+      launch_split_rows(Y, R, n3, n3, Ysp, true, nslices(plan), st);
+    }
+    LRTEI_TRY(tc_gemm(A, Ysp, nr, R, 1.0, Ju, R, false, false, s3, part, plan->d_status, st));
+  }
+  launch_unpack_J_range(plan->t, nbf, R, pair_begin, pair_end, Ju, pref, d_J, plan->d_status, st);
+  return finish_launch("apply X");
+}
+
 // Streamed J-builds: forced by LRTEI_JBUILD_BLOCK=<pairs per block>, else chosen when the
 // resident operands of the one-pass J-build would take more than half of the free device memory.
 static int64_t jbuild_stream_block(const lrtei_plan* plan) {

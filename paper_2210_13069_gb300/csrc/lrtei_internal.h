@@ -164,6 +164,9 @@ void launch_expand_B_rows(int nbf, const double* d_Bu, int64_t ldu, int64_t R0, 
 void launch_pack_density(int nbf, int R, const double* d_D, double* d_u, cudaStream_t st);
 // Unique-pair results -> full symmetric J: J_q(mu,nu) = J_q(nu,mu) = scale * Ju[r][q].
 void launch_unpack_J(int nbf, int R, const double* d_Ju, double scale, double* d_J, int* d_status, cudaStream_t st);
+// The unique pairs [r0, r1) only (Ju holds their rows); other entries of J are left as they are.
+void launch_unpack_J_range(const PairTable& t, int nbf, int R, int64_t r0, int64_t r1, const double* d_Ju, double scale,
+                           double* d_J, int* d_status, cudaStream_t st);
 
 // ---------------------------------------------------------------- Khatri-Rao compression
 // Scratch blocks of the Gram partial sums (d_part holds kr_gram_blocks * 3 * n * n doubles).

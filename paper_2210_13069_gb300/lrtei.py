@@ -83,6 +83,8 @@ def load():
         "lrtei_plan_compress": (S, [VP, ctypes.c_double, ctypes.c_int, DP, IP, VP]),
         "lrtei_jbuild": (S, [VP, VP, ctypes.c_int, VP, VP]),
         "lrtei_exchange": (S, [VP, VP, ctypes.c_int, VP, VP]),
+        "lrtei_jbuild_partial_x": (S, [VP, VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, VP, VP]),
+        "lrtei_jbuild_apply_x": (S, [VP, VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, VP, VP]),
         "lrtei_jbuild_batched": (S, [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(VP), IP, ctypes.POINTER(VP),
                                      VP]),
         "lrtei_selector_create": (S, [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(VP)]),
@@ -265,6 +267,16 @@ def lrtei_dense_K(plan: int, d_K, stream=None):
 
 def lrtei_jbuild(plan: int, d_D, R: int, d_J, stream=None):
     _check(load().lrtei_jbuild(plan, _ptr(d_D), int(R), _ptr(d_J), _stream(stream)))
+
+
+def lrtei_jbuild_partial_x(plan: int, d_D, R: int, pair_begin: int, pair_end: int, d_X, stream=None):
+    _check(load().lrtei_jbuild_partial_x(plan, _ptr(d_D), int(R), int(pair_begin), int(pair_end), _ptr(d_X),
+                                         _stream(stream)))
+
+
+def lrtei_jbuild_apply_x(plan: int, d_X, R: int, pair_begin: int, pair_end: int, d_J, stream=None):
+    _check(load().lrtei_jbuild_apply_x(plan, _ptr(d_X), int(R), int(pair_begin), int(pair_end), _ptr(d_J),
+                                       _stream(stream)))
 
 
 def lrtei_exchange(plan: int, d_Q, norb: int, d_K, stream=None):
