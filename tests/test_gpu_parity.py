@@ -570,6 +570,7 @@ def test_screening_matches_screened_oracle(lib, precision):
     assert err <= tol and errJ <= tol
     if precision == "fp64":
         S = pl.factors()[0].cpu().numpy()
+        Smax = np.abs(S).max(axis=(1, 2))  # the plan's largest moment in each dimension
         shell_of = [s for s, sh in enumerate(m.shells) for _ in range(sh.ncart)]
         row, nbf = 0, m.nbf
         for r, (mu, nu) in enumerate((mu, nu) for mu in range(nbf) for nu in range(mu, nbf)):
@@ -581,8 +582,12 @@ def test_screening_matches_screened_oracle(lib, precision):
                 want = np.array([W[j1 * Kn + j2] for j1, j2 in kept[r]])
                 got = S[d, row:row + len(kept[r])]
                 scale = np.abs(want).max(axis=1, keepdims=True)
-                # the two quadratures agree to 1e-13 of the row maximum, near-zero moments to rounding
-                assert np.all(np.abs(got - want) <= 1e-13 * scale + 1e-15), (mu, nu, d)
+                # the two quadratures agree to 1e-13 of the row maximum; a row whose largest moment
+                # is many orders below the plan's largest (a pair far from the box centre, with a
+                # small K_AB) enters B in that proportion, so its error is bounded against the plan's
+                # largest moment in this dimension instead (1e-16 of it: rounding)
+                floor = 1e-16 * Smax[d]
+                assert np.all(np.abs(got - want) <= 1e-13 * scale + floor), (mu, nu, d)
             row += len(kept[r])
         assert row == S.shape[1]
         p0 = lib.Plan(m, precision, tau_screening=0.0)
