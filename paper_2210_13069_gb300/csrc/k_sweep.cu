@@ -14,10 +14,16 @@
 
 namespace lrtei {
 
+// Ct holds each order's coefficients node-fastest, Ct[off + ((d n_c + a) n_c + b) P_c + p], so that
+// the threads of a warp (consecutive nodes p) read consecutive words.  For every dimension and
+// column primitive pair k a thread forms t = A_d^(p) S_d(k)^T once and reuses it for every row
+// primitive pair j (products over d accumulated per (j, k) when the pair block is small).
+constexpr int kOrdersMaxJK = 64;
+
 __global__ void __launch_bounds__(128) k_entries_orders(int n, int64_t nrows, const int64_t* __restrict__ pair_row,
                                                         const double* __restrict__ row_c, const double* __restrict__ S,
                                                         const int* __restrict__ cn, const int* __restrict__ cP,
-                                                        const int64_t* __restrict__ coff, const double* __restrict__ Call,
+                                                        const int64_t* __restrict__ coff, const double* __restrict__ Ct,
                                                         const double* __restrict__ wall, double pref,
                                                         const int64_t* __restrict__ rr, const int64_t* __restrict__ cc,
                                                         int64_t count, double* __restrict__ out, int* status) {
@@ -30,28 +36,53 @@ __global__ void __launch_bounds__(128) k_entries_orders(int n, int64_t nrows, co
     if (threadIdx.x == 0) out[(size_t)combo * count + e] = __longlong_as_double(0x7FF8000000000000LL);
     return;  // uniform across the block
   }
-  const double* C = Call + coff[combo];          // [3][Pc][nc][nc]
+  const double* C = Ct + coff[combo];  // [3][nc][nc][Pc]
   const double* w = wall + (size_t)combo * kMaxP;
   const int64_t j0 = pair_row[r], j1 = pair_row[r + 1], k0 = pair_row[c], k1 = pair_row[c + 1];
+  const int Ir = (int)(j1 - j0), Ic = (int)(k1 - k0);
   for (int p = threadIdx.x; p < Pc; p += blockDim.x) {
     double acc = 0.0;
-    for (int64_t j = j0; j < j1; ++j)
-      for (int64_t k = k0; k < k1; ++k) {
-        double prod = row_c[j] * row_c[k];
-        for (int d = 0; d < 3; ++d) {
-          const double* sj = S + ((size_t)d * nrows + j) * n;
-          const double* sk = S + ((size_t)d * nrows + k) * n;
-          const double* A = C + ((size_t)d * Pc + p) * nc * nc;
-          double g = 0.0;
+    if (Ir * Ic <= kOrdersMaxJK) {
+      double prod[kOrdersMaxJK];
+      for (int jk = 0; jk < Ir * Ic; ++jk) prod[jk] = row_c[j0 + jk / Ic] * row_c[k0 + jk % Ic];
+      for (int d = 0; d < 3; ++d) {
+        const double* A = C + (size_t)d * nc * nc * Pc + p;
+        for (int k = 0; k < Ic; ++k) {
+          const double* sk = S + ((size_t)d * nrows + k0 + k) * n;
+          double t[kMaxN];
           for (int a = 0; a < nc; ++a) {
-            double t = 0.0;
-            for (int b = 0; b < nc; ++b) t += A[a * nc + b] * sk[b];
-            g += sj[a] * t;
+            double x = 0.0;
+            for (int b = 0; b < nc; ++b) x += A[((size_t)a * nc + b) * Pc] * sk[b];
+            t[a] = x;
           }
-          prod *= g;
+          for (int j = 0; j < Ir; ++j) {
+            const double* sj = S + ((size_t)d * nrows + j0 + j) * n;
+            double g = 0.0;
+            for (int a = 0; a < nc; ++a) g += sj[a] * t[a];
+            prod[j * Ic + k] *= g;
+          }
         }
-        acc += prod;
       }
+      for (int jk = 0; jk < Ir * Ic; ++jk) acc += prod[jk];
+    } else {  // large pair blocks: one triple product per (j, k, d)
+      for (int64_t j = j0; j < j1; ++j)
+        for (int64_t k = k0; k < k1; ++k) {
+          double prod = row_c[j] * row_c[k];
+          for (int d = 0; d < 3; ++d) {
+            const double* sj = S + ((size_t)d * nrows + j) * n;
+            const double* sk = S + ((size_t)d * nrows + k) * n;
+            const double* A = C + (size_t)d * nc * nc * Pc + p;
+            double g = 0.0;
+            for (int a = 0; a < nc; ++a) {
+              double x = 0.0;
+              for (int b = 0; b < nc; ++b) x += A[((size_t)a * nc + b) * Pc] * sk[b];
+              g += sj[a] * x;
+            }
+            prod *= g;
+          }
+          acc += prod;
+        }
+    }
     term[p] = w[p] * acc;
   }
   __syncthreads();
@@ -114,7 +145,7 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
     for (void* q : mem) cudaFreeAsync(q, st);
     return rs;
   };
-  double *z, *w, *sn, *Call;
+  double *z, *w, *sn, *Call, *Ct;
   int *dn, *dP;
   int64_t *doff, *rr, *cc;
   cudaError_t e;
@@ -122,6 +153,7 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
       (e = get((void**)&w, sizeof(double) * (size_t)ncombo * kMaxP)) != cudaSuccess ||
       (e = get((void**)&sn, sizeof(double) * kMaxP)) != cudaSuccess ||
       (e = get((void**)&Call, sizeof(double) * (size_t)tot)) != cudaSuccess ||
+      (e = get((void**)&Ct, sizeof(double) * (size_t)tot)) != cudaSuccess ||
       (e = get((void**)&dn, sizeof(int) * ncombo)) != cudaSuccess ||
       (e = get((void**)&dP, sizeof(int) * ncombo)) != cudaSuccess ||
       (e = get((void**)&doff, sizeof(int64_t) * ncombo)) != cudaSuccess ||
@@ -139,11 +171,15 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
     launch_gauss_legendre(h_P[i], z, w + (size_t)i * kMaxP, st);
     launch_nodes_map(h_P[i], v.omega, z, sn, st);
     launch_cheb_coeff(h_n[i], h_P[i], sn, v.half3, Call + off[i], st);
+    const int64_t nn = (int64_t)h_n[i] * h_n[i];
+    for (int d = 0; d < 3; ++d)  // [p][a b] -> [a b][p] for each dimension
+      launch_transpose(Call + off[i] + (size_t)d * h_P[i] * nn, h_P[i], nn, nn, Ct + off[i] + (size_t)d * h_P[i] * nn,
+                       h_P[i], st);
   }
   launch_idx4_to_pairs(v.nbf, d_idx4, count, rr, cc, v.status, st);
   count_launch();
   k_entries_orders<<<dim3((unsigned)count, (unsigned)ncombo), 128, 0, st>>>(
-      v.n, v.t->nrows, v.t->pair_row, v.t->row_c, v.S, dn, dP, doff, Call, w, v.omega / sqrt(3.14159265358979323846),
+      v.n, v.t->nrows, v.t->pair_row, v.t->row_c, v.S, dn, dP, doff, Ct, w, v.omega / sqrt(3.14159265358979323846),
       rr, cc, count, d_out, v.status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return done(cuda_fail(e, "entries_orders launch"));

@@ -1441,7 +1441,10 @@ lrtei_status lrtei_exchange(lrtei_plan* plan, const double* d_Q, int norb, doubl
     LRTEI_TRY(scratch_split(sc, Xsp, (int64_t)ob * nbf, n3, false, plan));
     LRTEI_TRY(scratch_split(sc, Ypsp, nbf, (int64_t)ob * n3, false, plan));
     LRTEI_TRY(scratch_split(sc, Xpsp, nbf, (int64_t)ob * n3, true, plan));
-    const int sK = splits_for(nbf, (int64_t)ob * n3);
+    // split-K partials of the last product: the largest split count of any block (a shorter last
+    // block can take more splits than a full one)
+    const int nlast = norb - (nblk - 1) * ob;
+    const int sK = std::max(splits_for(nbf, (int64_t)ob * n3), splits_for(nbf, (int64_t)nlast * n3));
     double* part;
     LRTEI_TRY(sc.get(&part, (size_t)sK * nbf * nbf));
     {
@@ -1475,8 +1478,10 @@ lrtei_status lrtei_exchange(lrtei_plan* plan, const double* d_Q, int norb, doubl
         launch_split_rows(Yp, nbf, (int64_t)nj * n3, (int64_t)nj * n3, Ya, false, nslices(plan), st);
         launch_split_rows(Xp, nbf, (int64_t)nj * n3, (int64_t)nj * n3, Xa, true, nslices(plan), st);
       }
-      LRTEI_TRY(tc_gemm(Ya, Xa, nbf, nbf, 2.0, Kb + (size_t)b * nbf * nbf, nbf, false, false,
-                        splits_for(nbf, (int64_t)nj * n3), part, plan->d_status, st));
+      const int sb = splits_for(nbf, (int64_t)nj * n3);
+      if (sb > sK) { set_error("exchange: split count %d beyond the partial buffer's %d", sb, sK); return LRTEI_ERR_CUDA; }
+      LRTEI_TRY(tc_gemm(Ya, Xa, nbf, nbf, 2.0, Kb + (size_t)b * nbf * nbf, nbf, false, false, sb, part,
+                        plan->d_status, st));
     }
   } else {
     double *t1, *t2;

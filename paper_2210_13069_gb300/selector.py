@@ -180,3 +180,51 @@ class Selector:
         sel = cls(hidden=hidden, handle=h)
         sel.meta = json.loads(meta) if meta else {}
         return sel
+
+
+# ------------------------------------------------------------------ training run
+
+DEFAULT_CHECKPOINT = "selector_20k.bin"
+
+
+def train_from_sweeps(nsweeps: int, seed0: int = 10_000, epochs: int = 60, hidden: int = 64, net_seed: int = 11,
+                      log=print):
+    """Error sweeps of instances seed0 .. seed0 + nsweeps - 1, their labels, and a network trained
+    on them; returns (selector, number of labelled rows, loss history)."""
+    import time
+    t0 = time.perf_counter()
+    sweeps = []
+    for i in range(nsweeps):
+        sweeps.append(sweep(seed0 + i))
+        if log and (i + 1) % 1000 == 0:
+            log(f"  {i + 1} sweeps, {time.perf_counter() - t0:.0f} s")
+    X, Y = dataset(sweeps)
+    sel = Selector(hidden, seed=net_seed)
+    hist = sel.train(X, Y, epochs=epochs, batch=256, lr=2e-3)
+    if log:
+        log(f"{nsweeps} sweeps in {time.perf_counter() - t0:.0f} s, {len(X)} labelled rows, loss {hist[0]:.2e} -> "
+            f"{hist[-1]:.2e}")
+    return sel, len(X), hist
+
+
+def main(argv=None):
+    """python -m paper_2210_13069_gb300.selector --sweeps N --out FILE: train on N sweeps (seeds
+    10000..) and write the checkpoint (the library's versioned, checksummed format)."""
+    import argparse
+    import os
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sweeps", type=int, default=20_000)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), DEFAULT_CHECKPOINT))
+    a = ap.parse_args(argv)
+    from . import build_lib
+    build_lib.build()
+    sel, rows, hist = train_from_sweeps(a.sweeps, epochs=a.epochs)
+    sel.save(a.out, meta={"sweeps": a.sweeps, "first_seed": 10_000, "rows": rows, "epochs": a.epochs,
+                          "final_loss": float(hist[-1]), "n_grid": N_GRID, "p_grid": P_GRID,
+                          "reference": [N_REF, P_REF]})
+    print(f"wrote {a.out}")
+
+
+if __name__ == "__main__":
+    main()

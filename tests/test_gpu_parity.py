@@ -102,15 +102,16 @@ def mol_high_order(n, P, half, seed=2100):
 @pytest.mark.parametrize("n,P", [(40, 96), (56, 128), (64, 128)])
 def test_factors_and_B_rows_at_high_orders(lib, n, P, half):
     """Nodes, weights, Chebyshev coefficients and every moment row against the oracle (pinned at
-    n = 64 by QUADPACK) at n = 40..64 and P = 96..128, and sampled rows of the FP64 B by both
-    forms within 1e-12."""
+    n = 64 by QUADPACK) at n = 40..64 and P = 96..128, and sampled rows of the FP64 B within 1e-12:
+    by both forms at n = 40, by the Hadamard form above (the FP64 factored form's mode products
+    cost 6 P n^4 per row: minutes at n = 64)."""
     m = mol_high_order(n, P, half)
     o = oracle.Oracle.from_molecule(m)
     pl = lib.Plan(m, "fp64")
     S, C, s, w, c = [t.cpu().numpy() for t in pl.factors()]
     so, wo = o.nodes()
-    assert np.max(np.abs(s - so)) <= 1e-15 * m.omega
-    assert np.max(np.abs(w - wo) / wo) <= 1e-13
+    e_s = float(np.max(np.abs(s - so)) / m.omega)
+    e_w = float(np.max(np.abs(w - wo) / wo))
     worst_c = 0.0
     for d in range(3):
         for p in range(m.P):
@@ -128,13 +129,15 @@ def test_factors_and_B_rows_at_high_orders(lib, n, P, half):
     rows = [0, 7 * m.nbf + 12, (m.nbf - 1) * m.nbf + m.nbf - 1]
     ref = o.B_rows(rows)
     errs = {}
-    for form in ("hadamard", "factored"):
+    for form in ("hadamard", "factored") if n <= 40 else ("hadamard",):
         B = pl.assemble_B(form)
         errs[form] = rel_fro(B[rows].cpu().numpy(), ref)
         del B
     pl.status()
-    print(f"n={n} P={P} box half-width {half}: Chebyshev coefficients {worst_c:.1e}, moments {worst_s:.1e} "
-          f"(of each row's maximum), B rows {errs['hadamard']:.1e} / {errs['factored']:.1e}")
+    print(f"n={n} P={P} box half-width {half}: nodes {e_s:.1e}, weights {e_w:.1e}, Chebyshev coefficients "
+          f"{worst_c:.1e}, moments {worst_s:.1e} (of each row's maximum), B rows "
+          + ", ".join(f"{k} {v:.1e}" for k, v in errs.items()), flush=True)
+    assert e_s <= 1e-15 and e_w <= 1e-13
     assert worst_c <= 1e-14
     assert worst_s <= 1e-13
     assert max(errs.values()) <= 1e-12
