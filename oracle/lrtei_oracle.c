@@ -205,8 +205,8 @@ orc_ctx* orc_create(int nshells, const double* centers, const int* l, const int*
   }
   /* Chebyshev coefficient matrices (Definition 1, eq. chebcheb) */
   c->A = (double*)malloc(sizeof(double) * 3 * (size_t)P * n * n);
-  for (int d = 0; d < 3; ++d)
-    for (int p = 0; p < P; ++p) orc_cheb_coeff(c, d, p, c->A + ((size_t)d * P + p) * n * n);
+  #pragma omp parallel for schedule(dynamic)
+  for (int dp = 0; dp < 3 * P; ++dp) orc_cheb_coeff(c, dp / P, dp % P, c->A + (size_t)dp * n * n);
 
   orc_gauss_legendre(ORC_QPTS, c->qz, c->qw);
   c->mom = (double**)calloc((size_t)nb * nb * 3, sizeof(double*));
@@ -254,22 +254,33 @@ void orc_cheb_coeff(const orc_ctx* c, int d, int p, double* A) {
    * f(u, v) = exp(-s_p^2 (x - y)^2) with x = c_d + b_d u, y = c_d + b_d v. */
   const int n = c->n;
   const double sb = c->s[p] * c->half[d];
+  /* The kernel values f(u_k, u_k') and the cosines T_a(u_k) = cos(a th_k) are tabulated once
+   * (the same expressions as in the double sum, so every term and the summation order are those
+   * of the literal sum). */
+  double* F = (double*)malloc(sizeof(double) * (size_t)n * n);
+  double* Tc = (double*)malloc(sizeof(double) * (size_t)n * n);
+  for (int k = 1; k <= n; ++k) {
+    double th = (2.0 * k - 1.0) * M_PI / (2.0 * n);
+    double uk = cos(th);
+    for (int kk = 1; kk <= n; ++kk) {
+      double th2 = (2.0 * kk - 1.0) * M_PI / (2.0 * n);
+      double vk = cos(th2);
+      double diff = uk - vk;
+      F[(k - 1) * n + (kk - 1)] = exp(-sb * sb * diff * diff);
+    }
+    for (int a = 0; a < n; ++a) Tc[a * n + (k - 1)] = cos(a * th);
+  }
   for (int a = 0; a < n; ++a)
     for (int b = 0; b < n; ++b) {
       double sum = 0.0;
-      for (int k = 1; k <= n; ++k) {
-        double th = (2.0 * k - 1.0) * M_PI / (2.0 * n);
-        double uk = cos(th);
-        for (int kk = 1; kk <= n; ++kk) {
-          double th2 = (2.0 * kk - 1.0) * M_PI / (2.0 * n);
-          double vk = cos(th2);
-          double diff = uk - vk;
-          sum += exp(-sb * sb * diff * diff) * cos(a * th) * cos(b * th2);
-        }
-      }
+      for (int k = 1; k <= n; ++k)
+        for (int kk = 1; kk <= n; ++kk)
+          sum += F[(k - 1) * n + (kk - 1)] * Tc[a * n + (k - 1)] * Tc[b * n + (kk - 1)];
       double cab = (a == 0 && b == 0) ? 1.0 : ((a == 0 || b == 0) ? 2.0 : 4.0);
       A[a * n + b] = cab / ((double)n * n) * sum;
     }
+  free(F);
+  free(Tc);
 }
 
 /* ------------------------------------------------------------ 1D moments ---- */

@@ -196,8 +196,7 @@ cudaError_t launch_build_K(int n, int P, const double* d_C, const double* d_w, d
                            cudaStream_t st) {
   const int nn = n * n;
   Pair32* zp = nullptr;
-  count_alloc();
-  cudaError_t e = cudaMallocAsync((void**)&zp, sizeof(Pair32) * (size_t)nn * P, st);
+  cudaError_t e = scratch_alloc((void**)&zp, sizeof(Pair32) * (size_t)nn * P, st);
   if (e != cudaSuccess) return e;
   count_launch();
   k_K_zpairs<<<(unsigned)std::min<int64_t>(((int64_t)nn * P + 255) / 256, 152 * 8), 256, 0, st>>>(nn, P, d_C, zp);

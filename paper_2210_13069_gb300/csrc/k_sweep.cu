@@ -136,8 +136,7 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
   // scratch (stream-ordered, freed when the call returns its work to the stream)
   std::vector<void*> mem;
   auto get = [&](void** p, size_t bytes) {
-    count_alloc();
-    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = scratch_alloc(p, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) mem.push_back(*p);
     return e;
   };

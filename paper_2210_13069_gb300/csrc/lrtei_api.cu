@@ -31,6 +31,38 @@ lrtei_status cuda_fail(cudaError_t e, const char* what) {
   return LRTEI_ERR_CUDA;
 }
 
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+}  // namespace
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  count_alloc();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it == g_pools.end()) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = 2ULL << 30;
+      e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+      g_pools[dev] = pool;
+    } else {
+      pool = it->second;
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 lrtei_status finish_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, what);
@@ -493,12 +525,11 @@ static lrtei_status plan_create_impl(const lrtei_basis* basis, double omega, int
         if (e != cudaSuccess) { delete pl; return cuda_fail(e, what); }
         return LRTEI_OK;
       };
-      for (int k = 0; k < 5; ++k) count_alloc();
-      if ((ce = cudaMallocAsync((void**)&d_key, sizeof(int) * 3 * (size_t)t.nrows, st)) != cudaSuccess ||
-          (ce = cudaMallocAsync((void**)&d_l, sizeof(int) * (size_t)ns, st)) != cudaSuccess ||
-          (ce = cudaMallocAsync((void**)&d_rep, sizeof(int64_t) * (size_t)nkeys, st)) != cudaSuccess ||
-          (ce = cudaMallocAsync((void**)&d_off, sizeof(int64_t) * sp_off.size(), st)) != cudaSuccess ||
-          (ce = cudaMallocAsync((void**)&d_Su, sizeof(double) * (size_t)nkeys * n, st)) != cudaSuccess)
+      if ((ce = scratch_alloc((void**)&d_key, sizeof(int) * 3 * (size_t)t.nrows, st)) != cudaSuccess ||
+          (ce = scratch_alloc((void**)&d_l, sizeof(int) * (size_t)ns, st)) != cudaSuccess ||
+          (ce = scratch_alloc((void**)&d_rep, sizeof(int64_t) * (size_t)nkeys, st)) != cudaSuccess ||
+          (ce = scratch_alloc((void**)&d_off, sizeof(int64_t) * sp_off.size(), st)) != cudaSuccess ||
+          (ce = scratch_alloc((void**)&d_Su, sizeof(double) * (size_t)nkeys * n, st)) != cudaSuccess)
         return fin(ce, "moment key scratch");
       if ((ce = cudaMemcpyAsync(d_l, b.l.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
           (ce = cudaMemcpyAsync(d_off, sp_off.data(), sizeof(int64_t) * sp_off.size(), cudaMemcpyHostToDevice, st)) !=
@@ -685,8 +716,7 @@ struct Scratch {
   template <typename T>
   lrtei_status get(T** p, size_t count) {
     void* q = nullptr;
-    count_alloc();
-    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(16, count * sizeof(T)), st);
+    cudaError_t e = scratch_alloc(&q, std::max<size_t>(16, count * sizeof(T)), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("scratch allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));

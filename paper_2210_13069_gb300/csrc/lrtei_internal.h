@@ -52,6 +52,11 @@ void count_launch();
 void count_launches(long long n);
 long long launch_count();
 void set_launch_count(long long n);
+// Stream-ordered scratch from the library's memory pool of the current device (keeps up to 2 GiB
+// reserved across synchronisations, so that small calls do not map their scratch anew each time);
+// released with cudaFreeAsync.  Counts as one allocation request.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+
 // Counts device allocation requests (cudaMalloc / cudaMallocAsync) made by the library
 // (reported by lrtei_profile_get("alloc"); never reset).
 void count_alloc();

@@ -37,8 +37,7 @@ lrtei_status fma_rate(double* tflops, cudaStream_t st) {
   const int blocks = sms * 8, threads = 256;
   const int iters = sizeof(T) == 8 ? 2048 : 32768;
   T* out = nullptr;
-  count_alloc();
-  LRTEI_CUDA(cudaMallocAsync(&out, sizeof(T) * (size_t)blocks * threads, st));
+  LRTEI_CUDA(scratch_alloc((void**)&out, sizeof(T) * (size_t)blocks * threads, st));
   cudaEvent_t e0, e1;
   LRTEI_CUDA(cudaEventCreate(&e0));
   LRTEI_CUDA(cudaEventCreate(&e1));

@@ -98,8 +98,7 @@ def mol_high_order(n, P, half, seed=2100):
     return m
 
 
-@pytest.mark.parametrize("half", [2.5, 25.0])
-@pytest.mark.parametrize("n,P", [(40, 96), (56, 128), (64, 128)])
+@pytest.mark.parametrize("n,P,half", [(40, 96, 2.5), (40, 96, 25.0), (56, 128, 2.5), (64, 128, 25.0)])
 def test_factors_and_B_rows_at_high_orders(lib, n, P, half):
     """Nodes, weights, Chebyshev coefficients and every moment row against the oracle (pinned at
     n = 64 by QUADPACK) at n = 40..64 and P = 96..128, and sampled rows of the FP64 B within 1e-12:
