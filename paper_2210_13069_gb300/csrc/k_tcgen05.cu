@@ -694,6 +694,410 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
   return LRTEI_OK;
 }
 
+
+// ------------------------------------------------------------------ the 2-SM variant
+// cta_group::2: a cluster of two CTAs (on the two SMs of a TPC) computes a 256 x 128 tile of C.
+// Each CTA loads its own 128 rows of A and half of B (64 rows) into its shared memory; the
+// leader CTA (rank 0) issues M = 256, N = 128 MMAs that read A from both CTAs and both halves of
+// B, and write each CTA's 128 rows of the two accumulators into that CTA's TMEM.  Per 64-deep
+// stage an SM receives 80 KB (three 128-row A planes, four 64-row B planes) instead of 112 KB for
+// the same MMA work per SM.  Both CTAs' TMA loads complete on the leader's "full" barrier; the
+// leader's MMA commits arrive on both CTAs' "empty" and "accumulator ready" barriers (multicast);
+// both CTAs' epilogue warps arrive on the leader's "accumulator drained" barrier.  Six products,
+// 128 x 128 tiles per CTA, 64-deep stages, two stages; no symmetric walk.  Every wait is bounded
+// as in k_tc_gemm.
+namespace pair2 {
+constexpr int BN = 128;      // columns of the pair's tile (N of the MMA)
+constexpr int HB = BN / 2;   // B rows each CTA loads
+constexpr int BK = 64;
+constexpr int STAGES = 2;
+constexpr int kGroupM2 = 8;  // 256-row tiles walked together
+constexpr uint32_t A_BYTES = BM * BK * 2;          // one A plane (128 rows)
+constexpr uint32_t B_BYTES = HB * BK * 2;          // one B plane half (64 rows)
+constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
+constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 4 * 2 + (BM + BN) * 4;
+constexpr uint32_t RING_BYTES = (STAGES * STAGE_BYTES > TILE_BYTES) ? STAGES * STAGE_BYTES : TILE_BYTES;
+constexpr int EPI = 16;  // epilogue warps
+constexpr int THREADS = 64 + 32 * EPI;
+}  // namespace pair2
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_idx() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// TMA load into this CTA's shared memory, completing on an mbarrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, void* dst, uint32_t bar_cluster_addr, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster_addr)
+      : "memory");
+}
+template <ACol C>
+__device__ __forceinline__ void mma2_a(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  if constexpr (C == ACol::fill)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else if constexpr (C == ACol::use)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma2(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the same barrier offset in both CTAs of the pair once the MMAs issued so far retire
+__device__ __forceinline__ void mma2_commit_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+struct Work2 {
+  int64_t m0, n0;
+  int c_begin, nchunks;
+  int split;
+};
+
+__device__ __forceinline__ Work2 work_item2(const Params& p, int64_t item) {
+  Work2 w;
+  const int64_t tile = item % p.ntiles;
+  w.split = (int)(item / p.ntiles);
+  const int64_t per_group = (int64_t)pair2::kGroupM2 * p.tiles_n;
+  const int64_t first_m = (tile / per_group) * pair2::kGroupM2;
+  const int64_t gsize = min((int64_t)pair2::kGroupM2, p.tiles_m - first_m);
+  const int64_t in_g = tile % per_group;
+  w.m0 = (first_m + in_g % gsize) * (2 * BM);
+  w.n0 = (in_g / gsize) * pair2::BN;
+  w.c_begin = w.split * p.chunks_per_split;
+  w.nchunks = max(0, min(p.nchunks_total, w.c_begin + p.chunks_per_split) - w.c_begin);
+  return w;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair2::THREADS, 1)
+    k_tc_gemm_2sm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
+                  const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
+                  const __grid_constant__ CUtensorMap tb1, const __grid_constant__ CUtensorMap tb1h,
+                  const __grid_constant__ CUtensorMap tb2, const Params p) {
+  using namespace pair2;
+  constexpr int KSTEPS = KCHUNK / BK;
+  constexpr int QC = BN / (EPI / 4);  // columns per epilogue thread
+  constexpr int NE = 32 * EPI;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ((RING_BYTES + 7) & ~7u));
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;   // [2] accumulator buffer ready (both CTAs)
+  uint64_t* acce = accf + 2;         // [2] accumulator buffer drained (leader: both CTAs' epilogues)
+  uint64_t* done = acce + 2;         // all MMAs retired (both CTAs)
+  uint64_t* tstored = done + 1;      // this CTA's staged tile was stored
+  uint64_t* never = tstored + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const bool leader = rank == 0;
+  const int64_t nitems = p.ntiles * (int64_t)p.splits;
+  const int64_t cid = cluster_idx(), ncl = cluster_count();
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 2 * EPI);
+    }
+    mbar_init(done, 1);
+    mbar_init(tstored, EPI);
+    mbar_init(never, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers are initialised before any remote arrival
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t full_l0 = map_rank(smem_u32(&full[0]), 0);  // the leader's full barriers
+  const uint32_t acce_l0 = map_rank(smem_u32(&acce[0]), 0);  // the leader's drained barriers
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer (both CTAs)
+    if (lane == 0) {
+      uint32_t it = 0, ntile = 0;
+      bool stop = false;
+      for (int64_t item = cid; item < nitems && !stop; item += ncl, ++ntile) {
+        if (ntile > 0) {
+          if (!mbar_wait(tstored, (ntile - 1) & 1u, abort_flag, p.status, 64)) break;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        const Work2 w = work_item2(p, item);
+        const int nk = w.nchunks * KSTEPS;
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, 32)) { stop = true; break; }
+          if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);  // both CTAs' bytes
+          uint8_t* st = smem + (size_t)s * STAGE_BYTES;
+          uint8_t* sb = st + NA * A_BYTES;
+          const uint32_t fb = full_l0 + (uint32_t)(s * sizeof(uint64_t));
+          const int kx = (w.c_begin * KSTEPS + kk) * BK;
+          const int ay = (int)(w.m0 + rank * BM);
+          const int by = (int)(w.n0 + rank * HB);
+          tma_load_2d_pair(&ta0, st + 0 * A_BYTES, fb, kx, ay);
+          tma_load_2d_pair(&ta1, st + 1 * A_BYTES, fb, kx, ay);
+          tma_load_2d_pair(&ta2, st + 2 * A_BYTES, fb, kx, ay);
+          tma_load_2d_pair(&tb0, sb + 0 * B_BYTES, fb, kx, by);
+          tma_load_2d_pair(&tb1, sb + 1 * B_BYTES, fb, kx, by);
+          tma_load_2d_pair(&tb1h, sb + 2 * B_BYTES, fb, kx, by);
+          tma_load_2d_pair(&tb2, sb + 3 * B_BYTES, fb, kx, by);
+        }
+      }
+      // On abort the leader waits (bounded) for the stages in flight: they complete only when both
+      // CTAs' loads have landed.
+      if (*abort_flag && leader) {
+        for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0u); j < it; ++j) {
+          const int s = (int)(j % STAGES);
+          long long t0 = clock64();
+          while (!mbar_try_wait(&full[s], (j / STAGES) & 1u) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer (leader only)
+    if (lane == 0 && leader) {
+      // M = 256 (two CTAs), N = 128, FP16 operands, FP32 accumulators, both K-major
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+      uint32_t it = 0, cg = 0;
+      bool ok = true;
+      if (p.test_stall > 0) ok = mbar_wait(never, 0u, abort_flag, p.status, 0, p.test_stall);
+      for (int64_t item = cid; item < nitems && ok; item += ncl) {
+        const Work2 w = work_item2(p, item);
+        for (int c = 0; c < w.nchunks && ok; ++c, ++cg) {
+          const int buf = (int)(cg & 1u);
+          if (!mbar_wait(&acce[buf], ((cg >> 1) & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d0 = tmem_base + (uint32_t)(buf * 2 * BN);
+          const uint32_t d1 = d0 + BN;
+          for (int step = 0; step < KSTEPS; ++step, ++it) {
+            const int s = (int)(it % STAGES);
+            if (!mbar_wait(&full[s], (it / STAGES) & 1u, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
+            const uint64_t a0 = smem_desc<BK>(base), a1 = smem_desc<BK>(base + A_BYTES),
+                           a2 = smem_desc<BK>(base + 2 * A_BYTES);
+            const uint32_t bb = base + NA * A_BYTES;
+            const uint64_t b0 = smem_desc<BK>(bb), b1 = smem_desc<BK>(bb + B_BYTES),
+                           b1h = smem_desc<BK>(bb + 2 * B_BYTES), b2 = smem_desc<BK>(bb + 3 * B_BYTES);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t o = (uint64_t)((k * 32) >> 4);
+              const uint32_t first = (step == 0 && k == 0) ? 0u : 1u;
+              mma2_a<ACol::fill>(d0, a0 + o, b0 + o, idesc, first);
+              mma2_a<ACol::use>(d1, a0 + o, b1 + o, idesc, first);
+              mma2_a<ACol::lastuse>(d1, a0 + o, b2 + o, idesc, 1u);
+              mma2_a<ACol::fill>(d1, a1 + o, b0 + o, idesc, 1u);
+              mma2_a<ACol::lastuse>(d1, a1 + o, b1h + o, idesc, 1u);
+              mma2(d1, a2 + o, b0 + o, idesc, 1u);
+            }
+            mma2_commit_both(&empty[s]);
+          }
+          if (!ok) break;
+          mma2_commit_both(&accf[buf]);
+        }
+      }
+      mma2_commit_both(done);
+      long long t0 = clock64();
+      while (!mbar_try_wait(done, 0u) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue warps (both CTAs)
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int col0 = (ew >> 2) * QC;
+    const int row = quad * 32 + lane;
+    const int et = threadIdx.x - 64;
+    constexpr int LDS = BN + 1;
+    int* st0 = reinterpret_cast<int*>(smem);
+    float* st12 = reinterpret_cast<float*>(st0 + BM * LDS);
+    int* sea = reinterpret_cast<int*>(st12 + BM * LDS);
+    int* seb = sea + BM;
+    uint32_t cg = 0;
+    bool ok = true;
+    for (int64_t item = cid; item < nitems && ok; item += ncl) {
+      const Work2 w = work_item2(p, item);
+      const int64_t m0 = w.m0 + rank * BM;  // this CTA's 128 rows
+      int T0[QC];
+      float T12[QC];
+#pragma unroll
+      for (int j = 0; j < QC; ++j) {
+        T0[j] = 0;
+        T12[j] = 0.f;
+      }
+      for (int c = 0; c < w.nchunks; ++c, ++cg) {
+        const int buf = (int)(cg & 1u);
+        int got = 1;
+        if (lane == 0) got = mbar_wait(&accf[buf], (cg >> 1) & 1u, abort_flag, p.status, 128) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 2 * BN + col0);
+#pragma unroll
+        for (int j0 = 0; j0 < QC; j0 += 8) {
+          uint32_t r[8], q[8];
+          tmem_ld8(tbase + j0, r);
+          tmem_ld8(tbase + BN + j0, q);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            T0[j0 + j] += __float2int_rn(__uint_as_float(r[j]));
+            T12[j0 + j] += __uint_as_float(q[j]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (leader) mbar_arrive(&acce[buf]);
+          else mbar_arrive_remote(acce_l0 + (uint32_t)(buf * sizeof(uint64_t)));
+        }
+      }
+      if (!ok || *abort_flag) break;
+#pragma unroll
+      for (int j = 0; j < QC; ++j) {
+        st0[row * LDS + col0 + j] = T0[j];
+        st12[row * LDS + col0 + j] = T12[j];
+      }
+      if (et < BM) sea[et] = (m0 + et < p.M) ? p.ea[m0 + et] : 0;
+      if (et < BN) seb[et] = (w.n0 + et < p.N) ? p.eb[w.n0 + et] : 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
+      double* Cs = p.C + (int64_t)w.split * p.split_stride;
+      if (!p.transpose_out) {
+        for (int idx = et; idx < BM * BN; idx += NE) {
+          const int r = idx / BN, c = idx % BN;
+          const int64_t gm = m0 + r, gn = w.n0 + c;
+          if (gm < p.M && gn < p.N)
+            Cs[gm * p.ldc + gn] = tile_value<false, false>(st0, st12, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
+        }
+      } else {
+        for (int idx = et; idx < BM * BN; idx += NE) {
+          const int c = idx / BM, r = idx % BM;
+          const int64_t gm = m0 + r, gn = w.n0 + c;
+          if (gm < p.M && gn < p.N)
+            Cs[gn * p.ldc + gm] = tile_value<false, false>(st0, st12, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
+      if (lane == 0) mbar_arrive(tstored);
+    }
+  }
+  __syncthreads();
+  // the leader's MMAs write this CTA's TMEM: wait (bounded) until they have all retired
+  if (!leader && threadIdx.x == 0) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(done, 0u) && clock64() - t0 < kWaitCycles) {
+    }
+  }
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+  }
+}
+
+static lrtei_status launch_tc_2sm(const SplitMatrix& A, const SplitMatrix& B, const Params& p0, cudaStream_t st) {
+  using namespace pair2;
+  CUtensorMap m[7];
+  const bool ok = encode_plane(&m[0], A.s0, A.rows, A.kpad, BM, false, BK) &&
+                  encode_plane(&m[1], A.s1, A.rows, A.kpad, BM, false, BK) &&
+                  encode_plane(&m[2], A.s2, A.rows, A.kpad, BM, false, BK) &&
+                  encode_plane(&m[3], B.s0, B.rows, B.kpad, HB, false, BK) &&
+                  encode_plane(&m[4], B.s1, B.rows, B.kpad, HB, false, BK) &&
+                  encode_plane(&m[5], B.s1h, B.rows, B.kpad, HB, false, BK) &&
+                  encode_plane(&m[6], B.s2, B.rows, B.kpad, HB, false, BK);
+  if (!ok) {
+    set_error("cuTensorMapEncodeTiled failed (2-SM GEMM operands)");
+    return LRTEI_ERR_CUDA;
+  }
+  Params p = p0;
+  p.tiles_m = (p.M + 2 * BM - 1) / (2 * BM);
+  p.tiles_n = (p.N + BN - 1) / BN;
+  p.ntiles = p.tiles_m * p.tiles_n;
+  const size_t smem = (size_t)RING_BYTES + 1024 + 256;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_2sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "2-SM tc_gemm smem attribute");
+    attr_set = true;
+  }
+  static int nsm = 0;
+  if (nsm <= 0) {
+    int dev = 0;
+    LRTEI_CUDA(cudaGetDevice(&dev));
+    LRTEI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t nitems = p.ntiles * (int64_t)p.splits;
+  const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(nitems, nsm / 2));
+  count_launch();
+  k_tc_gemm_2sm<<<(unsigned)(2 * nclusters), THREADS, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "2-SM tc_gemm launch");
+  return LRTEI_OK;
+}
+
 }  // namespace tc
 
 namespace tc {
@@ -869,7 +1273,14 @@ static lrtei_status tc_gemm_impl(const SplitMatrix& A, const SplitMatrix& B, int
     set_error("tc_gemm: the eight-product scheme needs the A operand's t1 / 2^11 plane");
     return LRTEI_ERR_ARG;
   }
-  lrtei_status s = tc::run_tuned(A, B, p, splits, BN, plain, st);
+  lrtei_status s;
+  const char* two = getenv("LRTEI_TC_2SM");
+  if (two && two[0] == '1' && !symmetric_upper && !plain && !A.eight && BN == 128 && B.s1h) {
+    ProfScope ps("tc_gemm", st);
+    s = tc::launch_tc_2sm(A, B, p, st);  // opt-in 2-SM variant (cta_group::2)
+  } else {
+    s = tc::run_tuned(A, B, p, splits, BN, plain, st);
+  }
   if (s != LRTEI_OK) return s;
   if (splits > 1) {
     if (transpose_out)

@@ -1,0 +1,98 @@
+"""The 2-SM tensor-core GEMM (cta_group::2: a CTA pair computes 256 x 128 tiles, each SM loading
+half of B) on the non-symmetric products, against the one-SM kernel and the oracle.
+LRTEI_TC_2SM=1 selects it for six-product GEMMs with 128-column tiles."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_13069_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2210_13069_gb300 import build_lib, lrtei
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build_lib.build()
+    lrtei.load()
+    return lrtei
+
+
+def mol_ragged(seed=2002):
+    m = synth.random_molecule(seed, natoms=3, cube=5.0, nprim=2, alpha_range=(0.2, 30.0), omega=0.5, n=10, P=10)
+    rng = np.random.default_rng(seed)
+    for i, sh in enumerate(m.shells):
+        k = 1 + (i % 3)
+        sh.exps = np.sort(np.exp(rng.uniform(np.log(0.2), np.log(30.0), size=k)))[::-1].copy()
+        sh.coefs = rng.uniform(0.1, 1.0, size=k)
+    return m
+
+
+def mol_spd4():
+    return synth.workload_spd(natoms=4)  # N_b = 60, n = 24: G is 1830 x 13 824 (eight 256-row tiles)
+
+
+@pytest.mark.parametrize("maker", [mol_ragged, mol_spd4])
+def test_two_sm_assembly_matches_oracle_and_one_sm(lib, maker, monkeypatch):
+    m = maker()
+    o = oracle.Oracle.from_molecule(m)
+    nbf = m.nbf
+    rows = [0, nbf + 3, (nbf // 2) * nbf + nbf // 3, nbf * nbf - 1]
+    ref = o.B_rows(rows)
+    monkeypatch.delenv("LRTEI_TC_2SM", raising=False)
+    p1 = lib.Plan(m, "split_f16")
+    B1 = p1.assemble_B().cpu().numpy()
+    p1.status()
+    p1.close()
+    monkeypatch.setenv("LRTEI_TC_2SM", "1")
+    p2 = lib.Plan(m, "split_f16")
+    B2 = p2.assemble_B().cpu().numpy()
+    p2.status()
+    p2.close()
+    e2, e1 = rel_fro(B2[rows], ref), rel_fro(B1[rows], ref)
+    d = float(np.max(np.abs(B2 - B1)) / np.abs(B1).max())
+    print(f"2-SM GEMM, N_b={nbf}: rows vs oracle {e2:.2e} (one SM {e1:.2e}); max |2-SM - one SM| / max {d:.1e}")
+    assert e2 <= 1e-7
+    assert rel_fro(B2, B1) <= 1e-7
+
+
+def test_two_sm_full_size_180(lib, monkeypatch):
+    import time
+    import torch
+    m = synth.workload_spd()
+    o = oracle.Oracle.from_molecule(m)
+    nbf = m.nbf
+    rows = [0, 37 * nbf + 101, nbf * nbf - 1]
+    ref = o.B_rows(rows)
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("LRTEI_TC_2SM", flag)
+        pl = lib.Plan(m, "split_f16")
+        B = pl.assemble_B()
+        pl.assemble_B(out=B)
+        torch.cuda.synchronize()
+        lib.lrtei_profile_reset()
+        lib.lrtei_profile_enable(True)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            pl.assemble_B(out=B)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 3
+        g_ms, g_n = lib.lrtei_profile_get("tc_gemm")
+        lib.lrtei_profile_enable(False)
+        lib.lrtei_profile_reset()
+        pl.status()
+        out[flag] = (B[rows].cpu().numpy(), dt, g_ms / max(g_n, 1))
+        pl.close()
+        del B
+        torch.cuda.empty_cache()
+    e = rel_fro(out["1"][0], ref)
+    print(f"2-SM full size: {out['1'][1] * 1e3:.1f} ms per B (one SM {out['0'][1] * 1e3:.1f} ms); tc_gemm per launch "
+          f"{out['1'][2]:.2f} ms (one SM {out['0'][2]:.2f} ms); rows vs oracle {e:.2e}")
+    assert e <= 1e-7
