@@ -2,8 +2,8 @@
 // Chebyshev coefficient matrices (Definition 1, eq. chebcheb), basis normalisation, the
 // primitive-pair table (Proposition 1) and the 1D moment matrices S_d (eq. defV).
 //
-// All of this is FP64 on the device.  The moment integrals are computed by an 8-panel,
-// 32-point Gauss-Legendre rule over the window |x - P| <= 9/sqrt(p) of each primitive-pair
+// All of this is FP64 on the device.  The moment integrals are computed by an 8-panel (16 above
+// n = 32), 32-point Gauss-Legendre rule over the window |x - P| <= 9/sqrt(p) of each primitive-pair
 // Gaussian, clipped to the box: one warp per (row, dimension), one lane per quadrature point.
 #include <math.h>
 
@@ -81,6 +81,7 @@ __global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3,
   extern __shared__ double sm[];
   double* Tm = sm;          // n x n
   double* G = sm + n * n;   // n x n : G(k, b) = sum_k' F(k, k') Tm(b, k')
+  double* Fk = G + n * n;   // n x n : the kernel values F(k, k'), one exp each
   const int d = blockIdx.x / P, p = blockIdx.x % P;
   const double pi = 3.141592653589793238;
   const double sb = s[p] * half3[d];
@@ -92,14 +93,17 @@ __global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3,
   }
   __syncthreads();
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    int k = t / n, b = t % n;
+    const int k = t / n, kk = t % n;
     const double uk = cos((2.0 * k + 1.0) * pi / (2.0 * n));
+    const double vk = cos((2.0 * kk + 1.0) * pi / (2.0 * n));
+    const double df = cross ? s[p] * (hx * uk - hy * vk) : sb * (uk - vk);
+    Fk[t] = exp(-df * df);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int k = t / n, b = t % n;
     double acc = 0.0;
-    for (int kk = 0; kk < n; ++kk) {
-      const double vk = cos((2.0 * kk + 1.0) * pi / (2.0 * n));
-      double df = cross ? s[p] * (hx * uk - hy * vk) : sb * (uk - vk);
-      acc += exp(-df * df) * Tm[b * n + kk];
-    }
+    for (int kk = 0; kk < n; ++kk) acc += Fk[k * n + kk] * Tm[b * n + kk];
     G[t] = acc;
   }
   __syncthreads();
@@ -115,7 +119,7 @@ __global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3,
 }
 
 void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, double* d_C, cudaStream_t st) {
-  size_t smem = 2 * sizeof(double) * n * n;
+  size_t smem = 3 * sizeof(double) * n * n;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   count_launch();
   k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_half3, nullptr, d_C);
@@ -123,7 +127,7 @@ void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, d
 
 void launch_cheb_coeff_cross(int n, int P, const double* d_s, const double* d_hx3, const double* d_hy3, double* d_C,
                              cudaStream_t st) {
-  size_t smem = 2 * sizeof(double) * n * n;
+  size_t smem = 3 * sizeof(double) * n * n;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   count_launch();
   k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_hx3, d_hy3, d_C);
@@ -255,9 +259,12 @@ __global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const dou
     const double reach = 9.0 / sqrt(p);
     const double wl = fmax(lo, Pc - reach), wh = fmin(hi, Pc + reach);
     if (wh > wl) {
-      const double hp = (wh - wl) / kMomentPanels;
+      // T_{n-1} oscillates across the box: above n = 32 the window takes twice the panels (the
+      // 32-point rule on a panel is exact to degree 63 of the polynomial factor times T_m)
+      const int npan = n <= 32 ? kMomentPanels : 2 * kMomentPanels;
+      const double hp = (wh - wl) / npan;
       const double zq = gz[lane], wq = gw[lane];
-      for (int pan = 0; pan < kMomentPanels; ++pan) {
+      for (int pan = 0; pan < npan; ++pan) {
         const double mid = wl + (pan + 0.5) * hp;
         const double x = mid + 0.5 * hp * zq;
         const double dx = x - Pc;
