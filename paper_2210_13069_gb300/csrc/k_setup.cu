@@ -16,20 +16,31 @@ namespace lrtei {
 // ------------------------------------------------------------------ Gauss-Legendre ----
 // One thread per root.  Initial guess from Tricomi's asymptotic formula, Newton steps on the
 // Legendre polynomial with its derivative carried along the three-term recurrence
-// (P'_k = k P_{k-1} + x P'_{k-1}), weight 2 / ((1 - x)(1 + x) P'_N(x)^2).  (The equivalent form
+// (P'_k = k P_{k-1} + x P'_{k-1}), weight 2 / ((1 - x)(1 + x) P'_N(x)^2).  The recurrence is taken
+// as P_k = x P_{k-1} + q_k (x P_{k-1} - P_{k-2}) with q_k = (k - 1) / k tabulated per block, so that
+// no FP64 division runs inside the loop.  (The equivalent form
 // 2 (1 - x^2) / (N P_{N-1}(x))^2 loses digits at the outermost nodes for large N: 8e-12 relative at
 // N = 96, 4e-11 at N = 128, against 1e-13 for the derivative recurrence.)
+constexpr int kMaxGL = 256;  // largest rule k_gauss_legendre tabulates q_k for
+
 __global__ void k_gauss_legendre(int N, double* z, double* w) {
+  __shared__ double q[kMaxGL + 1];
+  for (int k = threadIdx.x; k <= N && k <= kMaxGL; k += blockDim.x) q[k] = k >= 1 ? (double)(k - 1) / k : 0.0;
+  __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double pi = 3.141592653589793238;
   double th = pi * (4.0 * (i + 1) - 1.0) / (4.0 * N + 2.0);
   double x = (1.0 - 1.0 / (8.0 * N * N) + 1.0 / (8.0 * N * N * N)) * cos(th);
   double dp = 1.0;
+  // Newton converges quadratically: once a step is below 1e-11 the next one leaves an error far
+  // below rounding, so one more step ends the iteration (the 100-step cap only bounds the loop)
+  bool last = false;
   for (int it = 0; it < 100; ++it) {
     double a = 1.0, b = x, db = 1.0;  // P_0, P_1, P_1'
     for (int k = 2; k <= N; ++k) {
-      const double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+      const double xb = x * b;
+      const double c = fma(q[k], xb - a, xb);
       const double dc = k * b + x * db;
       a = b;
       b = c;
@@ -39,12 +50,14 @@ __global__ void k_gauss_legendre(int N, double* z, double* w) {
     dp = (N == 0) ? 0.0 : db;
     const double dx = pn / dp;
     x -= dx;
-    if (fabs(dx) <= 1e-16 * fabs(x) + 1e-300) break;
+    if (last || dx == 0.0) break;
+    last = fabs(dx) <= 1e-11;
   }
   {
     double a = 1.0, b = x, db = 1.0;
     for (int k = 2; k <= N; ++k) {
-      const double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+      const double xb = x * b;
+      const double c = fma(q[k], xb - a, xb);
       const double dc = k * b + x * db;
       a = b;
       b = c;
@@ -58,6 +71,7 @@ __global__ void k_gauss_legendre(int N, double* z, double* w) {
 }
 
 void launch_gauss_legendre(int N, double* d_z, double* d_w, cudaStream_t st) {
+  if (N < 1 || N > kMaxGL) return;  // callers keep N <= kMaxP (128) and the 32-point panel rule
   count_launch();
   k_gauss_legendre<<<(N + 63) / 64, 64, 0, st>>>(N, d_z, d_w);
 }
@@ -204,7 +218,7 @@ __global__ void k_pair_rows(int64_t npair, const int* pair_mu, const int* pair_n
     row_p[row] = p;
     for (int d = 0; d < 3; ++d) {
       const double A = shell_center[3 * sm + d], B = shell_center[3 * sn + d];
-      row_P[d * nrows + row] = (a * A + b * B) / p;
+      row_P[d * nrows + row] = A + b / p * (B - A);  // exactly A for one centre
       row_K[d * nrows + row] = exp(-a * b / p * (A - B) * (A - B));
       row_A[d * nrows + row] = A;
       row_B[d * nrows + row] = B;

@@ -148,7 +148,7 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
   int *dn, *dP;
   int64_t *doff, *rr, *cc;
   cudaError_t e;
-  if ((e = get((void**)&z, sizeof(double) * kMaxP)) != cudaSuccess ||
+  if ((e = get((void**)&z, sizeof(double) * (size_t)ncombo * kMaxP)) != cudaSuccess ||
       (e = get((void**)&w, sizeof(double) * (size_t)ncombo * kMaxP)) != cudaSuccess ||
       (e = get((void**)&sn, sizeof(double) * kMaxP)) != cudaSuccess ||
       (e = get((void**)&Call, sizeof(double) * (size_t)tot)) != cudaSuccess ||
@@ -166,9 +166,21 @@ extern "C" lrtei_status lrtei_entries_orders(lrtei_plan* plan, int ncombo, const
       (e = cudaMemcpyAsync(dP, h_P, sizeof(int) * ncombo, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * ncombo, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return done(cuda_fail(e, "entries_orders upload"));
+  std::vector<int> first(kMaxP + 1, -1);  // first order with each P: its rule serves the others
   for (int i = 0; i < ncombo; ++i) {  // nodes, weights and Chebyshev coefficients of each order
-    launch_gauss_legendre(h_P[i], z, w + (size_t)i * kMaxP, st);
-    launch_nodes_map(h_P[i], v.omega, z, sn, st);
+    double* zi = z + (size_t)i * kMaxP;
+    double* wi = w + (size_t)i * kMaxP;
+    const int f = first[h_P[i]];
+    if (f < 0) {
+      first[h_P[i]] = i;
+      launch_gauss_legendre(h_P[i], zi, wi, st);
+    } else {
+      zi = z + (size_t)f * kMaxP;
+      if ((e = cudaMemcpyAsync(wi, w + (size_t)f * kMaxP, sizeof(double) * h_P[i], cudaMemcpyDeviceToDevice, st)) !=
+          cudaSuccess)
+        return done(cuda_fail(e, "entries_orders weights"));
+    }
+    launch_nodes_map(h_P[i], v.omega, zi, sn, st);
     launch_cheb_coeff(h_n[i], h_P[i], sn, v.half3, Call + off[i], st);
     const int64_t nn = (int64_t)h_n[i] * h_n[i];
     for (int d = 0; d < 3; ++d)  // [p][a b] -> [a b][p] for each dimension

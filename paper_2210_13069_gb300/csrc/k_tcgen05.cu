@@ -709,16 +709,21 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
 namespace pair2 {
 constexpr int BN = 128;      // columns of the pair's tile (N of the MMA)
 constexpr int HB = BN / 2;   // B rows each CTA loads
-constexpr int BK = 64;
-constexpr int STAGES = 2;
 constexpr int kGroupM2 = 8;  // 256-row tiles walked together
-constexpr uint32_t A_BYTES = BM * BK * 2;          // one A plane (128 rows)
-constexpr uint32_t B_BYTES = HB * BK * 2;          // one B plane half (64 rows)
-constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
 constexpr uint32_t TILE_BYTES = BM * (BN + 1) * 4 * 2 + (BM + BN) * 4;
-constexpr uint32_t RING_BYTES = (STAGES * STAGE_BYTES > TILE_BYTES) ? STAGES * STAGE_BYTES : TILE_BYTES;
 constexpr int EPI = 16;  // epilogue warps
 constexpr int THREADS = 64 + 32 * EPI;
+// stage depth BK and count: 64-deep (128-byte swizzle) x 2 or 32-deep (64-byte swizzle) x 5
+template <int BK>
+__host__ __device__ constexpr uint32_t a_bytes() { return BM * BK * 2; }  // one A plane (128 rows)
+template <int BK>
+__host__ __device__ constexpr uint32_t b_bytes() { return HB * BK * 2; }  // one B plane half (64 rows)
+template <int BK>
+__host__ __device__ constexpr uint32_t stage_bytes() { return NA * a_bytes<BK>() + NB * b_bytes<BK>(); }
+template <int BK, int STAGES>
+__host__ __device__ constexpr uint32_t ring_bytes() {
+  return (STAGES * stage_bytes<BK>() > TILE_BYTES) ? STAGES * stage_bytes<BK>() : TILE_BYTES;
+}
 }  // namespace pair2
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -800,12 +805,41 @@ struct Work2 {
   int64_t m0, n0;
   int c_begin, nchunks;
   int split;
+  int64_t cblk;  // symmetric product: the 128-column block of the tile
 };
 
+// Item -> tile.  Non-symmetric: groups of kGroupM2 256-row tiles, M fastest.  Symmetric (the upper
+// triangle of 128 x 128 blocks, block rows [blk0, blk1), blk0 even): pairs of block rows
+// (2i, 2i + 1) and the column blocks c >= 2i, in groups of kGroupM2 pairs, column by column; the
+// lower CTA's block (2i + 1, 2i) lies below the diagonal and is not stored.
 __device__ __forceinline__ Work2 work_item2(const Params& p, int64_t item) {
   Work2 w;
   const int64_t tile = item % p.ntiles;
   w.split = (int)(item / p.ntiles);
+  if (p.symmetric) {
+    const int64_t nb = (p.N + BM - 1) / BM;
+    const int64_t P0 = p.blk0 / 2, P1 = (p.blk1 + 1) / 2;
+    int64_t t = tile, pi = P0, c = 2 * P0;
+    for (int64_t G0 = P0; G0 < P1; G0 += pair2::kGroupM2) {
+      const int64_t G1 = min(P1, G0 + (int64_t)pair2::kGroupM2);
+      int64_t in_group = 0;
+      for (int64_t cc = 2 * G0; cc < nb; ++cc) in_group += max((int64_t)0, min(G1, cc / 2 + 1) - G0);
+      if (t >= in_group) { t -= in_group; continue; }
+      for (c = 2 * G0; c < nb; ++c) {
+        const int64_t rows_here = max((int64_t)0, min(G1, c / 2 + 1) - G0);
+        if (t < rows_here) { pi = G0 + t; break; }
+        t -= rows_here;
+      }
+      break;
+    }
+    w.m0 = pi * (2 * BM);
+    w.n0 = c * pair2::BN;
+    w.cblk = c;
+    w.c_begin = 0;
+    w.nchunks = p.nchunks_total;
+    return w;
+  }
+  w.cblk = 0;
   const int64_t per_group = (int64_t)pair2::kGroupM2 * p.tiles_n;
   const int64_t first_m = (tile / per_group) * pair2::kGroupM2;
   const int64_t gsize = min((int64_t)pair2::kGroupM2, p.tiles_m - first_m);
@@ -817,12 +851,15 @@ __device__ __forceinline__ Work2 work_item2(const Params& p, int64_t item) {
   return w;
 }
 
+template <int BK, int STAGES>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair2::THREADS, 1)
     k_tc_gemm_2sm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
                   const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
                   const __grid_constant__ CUtensorMap tb1, const __grid_constant__ CUtensorMap tb1h,
                   const __grid_constant__ CUtensorMap tb2, const Params p) {
   using namespace pair2;
+  constexpr uint32_t A_BYTES = a_bytes<BK>(), B_BYTES = b_bytes<BK>(), STAGE_BYTES = stage_bytes<BK>();
+  constexpr uint32_t RING_BYTES = ring_bytes<BK, STAGES>();
   constexpr int KSTEPS = KCHUNK / BK;
   constexpr int QC = BN / (EPI / 4);  // columns per epilogue thread
   constexpr int NE = 32 * EPI;
@@ -893,7 +930,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair2::THREADS, 1)
           uint8_t* sb = st + NA * A_BYTES;
           const uint32_t fb = full_l0 + (uint32_t)(s * sizeof(uint64_t));
           const int kx = (w.c_begin * KSTEPS + kk) * BK;
-          const int ay = (int)(w.m0 + rank * BM);
+          const int ay = (int)(w.m0 + rank * BM - p.a_row0);
           const int by = (int)(w.n0 + rank * HB);
           tma_load_2d_pair(&ta0, st + 0 * A_BYTES, fb, kx, ay);
           tma_load_2d_pair(&ta1, st + 1 * A_BYTES, fb, kx, ay);
@@ -1020,11 +1057,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair2::THREADS, 1)
         st0[row * LDS + col0 + j] = T0[j];
         st12[row * LDS + col0 + j] = T12[j];
       }
-      if (et < BM) sea[et] = (m0 + et < p.M) ? p.ea[m0 + et] : 0;
+      if (et < BM) sea[et] = (m0 + et < p.M) ? p.ea[m0 - p.a_row0 + et] : 0;
       if (et < BN) seb[et] = (w.n0 + et < p.N) ? p.eb[w.n0 + et] : 0;
       asm volatile("bar.sync 1, %0;" ::"r"(NE) : "memory");
       double* Cs = p.C + (int64_t)w.split * p.split_stride;
-      if (!p.transpose_out) {
+      if (p.symmetric) {
+        // this CTA's block (br, c): below the diagonal nothing is stored; on it the upper triangle
+        // is kept and mirrored, so that C comes out exactly symmetric; above it, block and mirror
+        const int64_t br = m0 / BM;
+        if (w.cblk >= br) {
+          const bool diag = w.cblk == br;
+          for (int idx = et; idx < BM * BN; idx += NE) {
+            const int r = idx / BN, c = idx % BN;
+            const int64_t gm = m0 + r, gn = w.n0 + c;
+            if (gm < p.M && gn < p.N && (!diag || gm <= gn))
+              Cs[gm * p.ldc + gn] = tile_value<false, false>(st0, st12, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
+          }
+          for (int idx = et; idx < BM * BN; idx += NE) {
+            const int c = idx / BM, r = idx % BM;
+            const int64_t gm = m0 + r, gn = w.n0 + c;
+            if (gm < p.M && gn < p.N && (!diag || gm < gn))
+              Cs[gn * p.ldc + gm] = tile_value<false, false>(st0, st12, st12, r * LDS + c, sea[r] + seb[c] - 16, p.scale);
+          }
+        }
+      } else if (!p.transpose_out) {
         for (int idx = et; idx < BM * BN; idx += NE) {
           const int r = idx / BN, c = idx % BN;
           const int64_t gm = m0 + r, gn = w.n0 + c;
@@ -1058,6 +1114,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair2::THREADS, 1)
   }
 }
 
+template <int BK, int STAGES>
 static lrtei_status launch_tc_2sm(const SplitMatrix& A, const SplitMatrix& B, const Params& p0, cudaStream_t st) {
   using namespace pair2;
   CUtensorMap m[7];
@@ -1076,10 +1133,16 @@ static lrtei_status launch_tc_2sm(const SplitMatrix& A, const SplitMatrix& B, co
   p.tiles_m = (p.M + 2 * BM - 1) / (2 * BM);
   p.tiles_n = (p.N + BN - 1) / BN;
   p.ntiles = p.tiles_m * p.tiles_n;
-  const size_t smem = (size_t)RING_BYTES + 1024 + 256;
+  if (p.symmetric) {  // pairs of block rows [blk0 / 2, ceil(blk1 / 2)), column blocks c >= 2i
+    const int64_t nb = (p.N + BM - 1) / BM;
+    p.ntiles = 0;
+    for (int64_t i = p.blk0 / 2; i < (p.blk1 + 1) / 2; ++i) p.ntiles += std::max<int64_t>(0, nb - 2 * i);
+  }
+  const size_t smem = (size_t)ring_bytes<BK, STAGES>() + 1024 + 256;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_2sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tc_gemm_2sm<BK, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "2-SM tc_gemm smem attribute");
     attr_set = true;
   }
@@ -1092,7 +1155,8 @@ static lrtei_status launch_tc_2sm(const SplitMatrix& A, const SplitMatrix& B, co
   const int64_t nitems = p.ntiles * (int64_t)p.splits;
   const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(nitems, nsm / 2));
   count_launch();
-  k_tc_gemm_2sm<<<(unsigned)(2 * nclusters), THREADS, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], p);
+  k_tc_gemm_2sm<BK, STAGES><<<(unsigned)(2 * nclusters), THREADS, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6],
+                                                                              p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "2-SM tc_gemm launch");
   return LRTEI_OK;
@@ -1274,10 +1338,16 @@ static lrtei_status tc_gemm_impl(const SplitMatrix& A, const SplitMatrix& B, int
     return LRTEI_ERR_ARG;
   }
   lrtei_status s;
+  // LRTEI_TC_2SM=1: the 2-SM variant for the non-symmetric products; =2: for the symmetric ones
+  // too (block bands starting on an even 128-row block)
   const char* two = getenv("LRTEI_TC_2SM");
-  if (two && two[0] == '1' && !symmetric_upper && !plain && !A.eight && BN == 128 && B.s1h) {
+  const bool two_ok = two && (two[0] == '1' || two[0] == '2') && !plain && !A.eight && BN == 128 && B.s1h &&
+                      (!symmetric_upper || (two[0] == '2' && p.blk0 % 2 == 0)) && p.M < (1LL << 31);
+  if (two_ok) {
     ProfScope ps("tc_gemm", st);
-    s = tc::launch_tc_2sm(A, B, p, st);  // opt-in 2-SM variant (cta_group::2)
+    // stage shape: LRTEI_TC_2SM_BK=64 selects two 64-deep stages, else five 32-deep ones
+    const char* bk = getenv("LRTEI_TC_2SM_BK");
+    s = (bk && atoi(bk) == 64) ? tc::launch_tc_2sm<64, 2>(A, B, p, st) : tc::launch_tc_2sm<32, 5>(A, B, p, st);
   } else {
     s = tc::run_tuned(A, B, p, splits, BN, plain, st);
   }

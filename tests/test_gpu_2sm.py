@@ -1,6 +1,7 @@
 """The 2-SM tensor-core GEMM (cta_group::2: a CTA pair computes 256 x 128 tiles, each SM loading
-half of B) on the non-symmetric products, against the one-SM kernel and the oracle.
-LRTEI_TC_2SM=1 selects it for six-product GEMMs with 128-column tiles."""
+half of B), against the one-SM kernel and the oracle.  LRTEI_TC_2SM=1 selects it for the
+non-symmetric six-product GEMMs with 128-column tiles (G = F_u K), =2 for the symmetric B_u = G F_u^T
+too; LRTEI_TC_2SM_BK=64 gives it two 64-deep operand stages instead of five 32-deep ones."""
 import numpy as np
 import pytest
 
@@ -38,8 +39,10 @@ def mol_spd4():
     return synth.workload_spd(natoms=4)  # N_b = 60, n = 24: G is 1830 x 13 824 (eight 256-row tiles)
 
 
+@pytest.mark.parametrize("bk", ["32", "64"])
+@pytest.mark.parametrize("flag", ["1", "2"])
 @pytest.mark.parametrize("maker", [mol_ragged, mol_spd4])
-def test_two_sm_assembly_matches_oracle_and_one_sm(lib, maker, monkeypatch):
+def test_two_sm_assembly_matches_oracle_and_one_sm(lib, maker, flag, bk, monkeypatch):
     m = maker()
     o = oracle.Oracle.from_molecule(m)
     nbf = m.nbf
@@ -50,16 +53,19 @@ def test_two_sm_assembly_matches_oracle_and_one_sm(lib, maker, monkeypatch):
     B1 = p1.assemble_B().cpu().numpy()
     p1.status()
     p1.close()
-    monkeypatch.setenv("LRTEI_TC_2SM", "1")
+    monkeypatch.setenv("LRTEI_TC_2SM", flag)
+    monkeypatch.setenv("LRTEI_TC_2SM_BK", bk)
     p2 = lib.Plan(m, "split_f16")
     B2 = p2.assemble_B().cpu().numpy()
     p2.status()
     p2.close()
     e2, e1 = rel_fro(B2[rows], ref), rel_fro(B1[rows], ref)
     d = float(np.max(np.abs(B2 - B1)) / np.abs(B1).max())
-    print(f"2-SM GEMM, N_b={nbf}: rows vs oracle {e2:.2e} (one SM {e1:.2e}); max |2-SM - one SM| / max {d:.1e}")
+    print(f"2-SM GEMM ({flag}, BK {bk}), N_b={nbf}: rows vs oracle {e2:.2e} (one SM {e1:.2e}); max |2-SM - one SM| / max "
+          f"{d:.1e}; symmetric {np.abs(B2 - B2.T).max():.1e}")
     assert e2 <= 1e-7
     assert rel_fro(B2, B1) <= 1e-7
+    assert np.array_equal(B2, B2.T)  # the symmetric walk mirrors every block exactly
 
 
 def test_two_sm_full_size_180(lib, monkeypatch):
@@ -71,8 +77,10 @@ def test_two_sm_full_size_180(lib, monkeypatch):
     rows = [0, 37 * nbf + 101, nbf * nbf - 1]
     ref = o.B_rows(rows)
     out = {}
-    for flag in ("0", "1"):
+    runs = [("0", "32"), ("1", "32"), ("1", "64"), ("2", "32"), ("2", "64")]
+    for flag, bk in runs:
         monkeypatch.setenv("LRTEI_TC_2SM", flag)
+        monkeypatch.setenv("LRTEI_TC_2SM_BK", bk)
         pl = lib.Plan(m, "split_f16")
         B = pl.assemble_B()
         pl.assemble_B(out=B)
@@ -88,11 +96,13 @@ def test_two_sm_full_size_180(lib, monkeypatch):
         lib.lrtei_profile_enable(False)
         lib.lrtei_profile_reset()
         pl.status()
-        out[flag] = (B[rows].cpu().numpy(), dt, g_ms / max(g_n, 1))
+        out[flag, bk] = (B[rows].cpu().numpy(), dt, g_ms / max(g_n, 1))
         pl.close()
         del B
         torch.cuda.empty_cache()
-    e = rel_fro(out["1"][0], ref)
-    print(f"2-SM full size: {out['1'][1] * 1e3:.1f} ms per B (one SM {out['0'][1] * 1e3:.1f} ms); tc_gemm per launch "
-          f"{out['1'][2]:.2f} ms (one SM {out['0'][2]:.2f} ms); rows vs oracle {e:.2e}")
-    assert e <= 1e-7
+    one = out["0", "32"]
+    for key in runs[1:]:
+        e = rel_fro(out[key][0], ref)
+        print(f"2-SM ({key[0]}, BK {key[1]}) full size: {out[key][1] * 1e3:.1f} ms per B (one SM {one[1] * 1e3:.1f} "
+              f"ms); tc_gemm per launch {out[key][2]:.2f} ms (one SM {one[2]:.2f} ms); rows vs oracle {e:.2e}")
+        assert e <= 1e-7
