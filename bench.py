@@ -183,6 +183,17 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def jbuild_operand_bytes(nbf: int, n: int, precision: str) -> float:
+    """Compulsory HBM reads of one factored J-build's three GEMMs (eq. coulapprox): F_u^T (for
+    X = F_u^T D), the dense K (Y = K X) and F_u (J_u = F_u Y), each read once as the GEMMs' A operand
+    in 16-bit planes (three planes for six products, four for eight, one for plain BF16); the
+    densities and the n^3-wide intermediates are negligible beside them."""
+    planes = {"split_f16_8": 4, "bf16": 1}.get(precision, 3)
+    npair = nbf * (nbf + 1) // 2
+    n3 = n ** 3
+    return 2.0 * planes * (2 * npair * n3 + n3 * n3)
+
+
 def kernel_source_hash(rel):
     h = hashlib.sha256()
     with open(os.path.join(ROOT, rel), "rb") as f:
@@ -437,8 +448,11 @@ def run_ours(args, world, rank, local):
             torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         jms = j0.elapsed_time(j1) / reps
+        jbytes = jbuild_operand_bytes(nbf, mol.n, args.precision)
         jb = {"value": world * R / (max_over_ranks(jms, world, device="cuda") / 1e3), "unit": "J-builds/s",
-              "densities": R, "ms_per_batch": jms}
+              "densities": R, "ms_per_batch": jms, "operand_bytes": jbytes,
+              "hbm_GBps": jbytes / (jms * 1e-3) / 1e9,
+              "hbm_frac": jbytes / (jms * 1e-3) / 1e9 / measured_peaks()[0]["hbm_gbs"]}
         del D, J
 
     # ---- end to end through the public API: host basis in, host B out.  The plan is created
@@ -744,6 +758,7 @@ def run_batched(args, world, budget_gb: float = 170.0):
     R = 16
     stream = torch.cuda.current_stream()
     total_ms, nj = 0.0, 0
+    tot_bytes = sum(jbuild_operand_bytes(m.nbf, m.n, args.precision) for m in mols)
     for g in groups:
         plans = [lrtei.Plan(mols[i], args.precision) for i in g]
         Ds = [torch.as_tensor(synth.random_densities(7000 + i, mols[i].nbf, R), device="cuda") for i in g]
@@ -770,6 +785,8 @@ def run_batched(args, world, budget_gb: float = 170.0):
     total_ms = max_over_ranks(total_ms, world, device="cuda")
     return {"value": world * nj / (total_ms / 1e3), "unit": "J-builds/s", "molecules": len(mols),
             "densities_each": R, "graph_launches_per_batch": len(groups), "ms_per_batch": total_ms,
+            "operand_bytes": tot_bytes, "hbm_GBps": tot_bytes / (total_ms * 1e-3) / 1e9,
+            "hbm_frac": tot_bytes / (total_ms * 1e-3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
             "note": "molecules grouped so that one group's operands fit in HBM; one graph launch per group"}
 
 

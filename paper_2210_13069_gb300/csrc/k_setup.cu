@@ -91,49 +91,84 @@ void launch_nodes_map(int P, double omega, const double* d_z, double* d_s, cudaS
 // F(k, k') = exp(-(s_p b_d)^2 (u_k - u_k')^2), alpha = (c_ab / n^2) (Tm F Tm^T)(a, b).
 // Two intervals (the adaptive boxes of Section 6): x = c + hx_d u on one side, y = c + hy_d v on
 // the other, F(k, k') = exp(-s_p^2 (hx_d u_k - hy_d u_k')^2); hy3 == NULL means hy3 = hx3.
+//
+// The first-kind grid is mirror-symmetric: node kb = n - 1 - k has u_kb = -u_k, so
+// T_a(u_kb) = (-1)^a T_a(u_k) and F(kb, kb') = F(k, k'), F(kb, k') = F(k, kb') (both intervals flip
+// together).  Folding the double sum over the mirror pairs k < h = floor(n/2) (plus the middle node
+// km = (n-1)/2, u = 0, when n is odd):
+//   Y_b(k) = sum_k' F(k, k') T_b(u_k') = sum_{k' < h} T_b(u_k') (F(k, k') + (-1)^b F(k, kb'))
+//            [+ T_b(0) F(k, km)],
+//   Y_b(kb) = (-1)^b Y_b(k), so alpha_ab = 0 when a + b is odd, and otherwise
+//   alpha_ab = (c_ab / n^2) (2 sum_{k < h} T_a(u_k) Y_b(k) [+ T_a(0) Y_b(km)]).
+// The same terms as the full double sum, regrouped: a quarter of its multiply-adds, half its exps.
 __global__ void k_cheb_coeff(int n, int P, const double* s, const double* half3, const double* hy3, double* C) {
   extern __shared__ double sm[];
-  double* Tm = sm;          // n x n
-  double* G = sm + n * n;   // n x n : G(k, b) = sum_k' F(k, k') Tm(b, k')
-  double* Fk = G + n * n;   // n x n : the kernel values F(k, k'), one exp each
+  const int h = n / 2, hh = (n + 1) / 2;  // mirror pairs; rows with the middle node
+  const bool odd = (n & 1) != 0;
+  double* Tm = sm;             // n x hh : T_a(u_k), k < hh
+  double* Fp = Tm + n * hh;    // hh x hh : F(k, k') + F(k, kb') (k' < h); F(k, km) in column km
+  double* Fm = Fp + hh * hh;   // hh x hh : F(k, k') - F(k, kb') (k' < h)
+  double* Y = Fm + hh * hh;    // hh x n : Y_b(k)
   const int d = blockIdx.x / P, p = blockIdx.x % P;
   const double pi = 3.141592653589793238;
   const double sb = s[p] * half3[d];
   const bool cross = hy3 != nullptr && hy3[d] != half3[d];
   const double hx = half3[d], hy = cross ? hy3[d] : hx;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    int a = t / n, k = t % n;
+  for (int t = threadIdx.x; t < n * hh; t += blockDim.x) {
+    const int a = t / hh, k = t % hh;
     Tm[t] = cos(a * (2.0 * k + 1.0) * pi / (2.0 * n));
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int k = t / n, kk = t % n;
+  for (int t = threadIdx.x; t < hh * hh; t += blockDim.x) {
+    const int k = t / hh, kk = t % hh;
     const double uk = cos((2.0 * k + 1.0) * pi / (2.0 * n));
     const double vk = cos((2.0 * kk + 1.0) * pi / (2.0 * n));
     const double df = cross ? s[p] * (hx * uk - hy * vk) : sb * (uk - vk);
-    Fk[t] = exp(-df * df);
+    const double f = exp(-df * df);
+    if (kk < h) {
+      const double vb = cos((2.0 * (n - 1 - kk) + 1.0) * pi / (2.0 * n));
+      const double dg = cross ? s[p] * (hx * uk - hy * vb) : sb * (uk - vb);
+      const double g = exp(-dg * dg);
+      Fp[t] = f + g;
+      Fm[t] = f - g;
+    } else {  // the middle node's column (n odd)
+      Fp[t] = f;
+      Fm[t] = 0.0;
+    }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    int k = t / n, b = t % n;
+  for (int t = threadIdx.x; t < hh * n; t += blockDim.x) {
+    const int k = t / n, b = t % n;
+    const double* F = (b & 1) ? Fm : Fp;
+    const int kend = (b & 1) ? h : hh;
     double acc = 0.0;
-    for (int kk = 0; kk < n; ++kk) acc += Fk[k * n + kk] * Tm[b * n + kk];
-    G[t] = acc;
+    for (int kk = 0; kk < kend; ++kk) acc += F[k * hh + kk] * Tm[b * hh + kk];
+    Y[t] = acc;
   }
   __syncthreads();
   double* out = C + (size_t)blockIdx.x * n * n;
   const double inv = 1.0 / ((double)n * n);
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    int a = t / n, b = t % n;
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc += Tm[a * n + k] * G[k * n + b];
-    double cab = (a == 0 ? 1.0 : 2.0) * (b == 0 ? 1.0 : 2.0);
-    out[t] = cab * inv * acc;
+    const int a = t / n, b = t % n;
+    double v = 0.0;
+    if (((a + b) & 1) == 0) {
+      double acc = 0.0;
+      for (int k = 0; k < h; ++k) acc += Tm[a * hh + k] * Y[k * n + b];
+      acc *= 2.0;
+      if (odd) acc += Tm[a * hh + h] * Y[h * n + b];
+      const double cab = (a == 0 ? 1.0 : 2.0) * (b == 0 ? 1.0 : 2.0);
+      v = cab * inv * acc;
+    }
+    out[t] = v;
   }
 }
 
+static size_t cheb_smem(int n) {
+  const size_t hh = (n + 1) / 2;
+  return sizeof(double) * (2 * n * hh + 2 * hh * hh);
+}
+
 void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, double* d_C, cudaStream_t st) {
-  size_t smem = 3 * sizeof(double) * n * n;
+  size_t smem = cheb_smem(n);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   count_launch();
   k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_half3, nullptr, d_C);
@@ -141,7 +176,7 @@ void launch_cheb_coeff(int n, int P, const double* d_s, const double* d_half3, d
 
 void launch_cheb_coeff_cross(int n, int P, const double* d_s, const double* d_hx3, const double* d_hy3, double* d_C,
                              cudaStream_t st) {
-  size_t smem = 3 * sizeof(double) * n * n;
+  size_t smem = cheb_smem(n);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cheb_coeff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   count_launch();
   k_cheb_coeff<<<3 * P, 256, smem, st>>>(n, P, d_s, d_hx3, d_hy3, d_C);
