@@ -116,6 +116,8 @@ struct lrtei_plan {
   float* d_F32 = nullptr;     // factored: npair * n^3 (FP32)
   SplitMatrix Fsp, Ksp, FTsp; // tensor-core operands: F_u, K, F_u^T as BF16 slices
   bool have_Fsp = false, have_Ksp = false, have_FTsp = false;
+  HadOperands had;            // tensor-core Hadamard form (one primitive pair per unique pair)
+  bool have_had = false;
   std::vector<void*> allocs;
   size_t bytes = 0;
 
@@ -1113,14 +1115,57 @@ lrtei_status jbuild_adaptive(lrtei_plan* pl, const double* d_D, int R, double* d
   return finish_launch("adaptive J-build");
 }
 
+// The tensor-core Hadamard form covers six-product split plans whose unique pairs each hold one
+// primitive pair (uncontracted bases), n <= 64, with the plain moments of one box.
+bool hadamard_tc_ok(const lrtei_plan* pl) {
+  return pl->prec == LRTEI_SPLIT_F16 && pl->t.nrows == pl->t.npair && pl->t.maxI == 1 && pl->n <= 64 &&
+         pl->kr_rank == 0 && pl->npart == 0 && 3LL * pl->P * pl->t.nrows < (1LL << 31);
+}
+
 int choose_form(const lrtei_plan* pl, lrtei_form form) {
-  if (is_split(pl)) return LRTEI_FORM_FACTORED;  // the tensor-core path runs the factored form
-  if (form == LRTEI_FORM_HADAMARD || form == LRTEI_FORM_FACTORED) return form;
-  // Hadamard: ~ npair^2 * P * Ibar^2 * (6n + 3); factored: ~ npair^2 n^3 + 6 P n^4 npair.
-  const double Ibar2 = (double)pl->t.nrows / pl->t.npair;
+  // Per element of B_u: Hadamard ~ P Ibar^2 (6n + 3); factored ~ 2 n^3 (+ 6 P n^4 per row).
+  const double Ibar2 = (double)pl->t.nrows / std::max<int64_t>(1, pl->t.npair);
   const double had = (double)pl->P * Ibar2 * Ibar2 * (6.0 * pl->n + 3.0);
   const double fac = (double)pl->n * pl->n * pl->n * 2.0;
+  if (is_split(pl)) {  // tensor cores: the factored form, or the Hadamard form where it applies
+    if (!hadamard_tc_ok(pl) || form == LRTEI_FORM_FACTORED) return LRTEI_FORM_FACTORED;
+    return (form == LRTEI_FORM_HADAMARD || had <= fac) ? LRTEI_FORM_HADAMARD : LRTEI_FORM_FACTORED;
+  }
+  if (form == LRTEI_FORM_HADAMARD || form == LRTEI_FORM_FACTORED) return form;
   return had <= fac ? LRTEI_FORM_HADAMARD : LRTEI_FORM_FACTORED;
+}
+
+// Slices of T_{d,p} and S'_d and the node tables of the tensor-core Hadamard form (once per plan).
+lrtei_status ensure_had(lrtei_plan* pl, cudaStream_t st) {
+  if (pl->have_had) return LRTEI_OK;
+  HadOperands& h = pl->had;
+  h.nrows = pl->t.nrows;
+  h.n = pl->n;
+  h.P = pl->P;
+  h.kpad = pl->n <= 32 ? 32 : 64;
+  const size_t tcnt = 3ULL * h.P * h.nrows * h.kpad, scnt = 3ULL * h.nrows * h.kpad;
+  LRTEI_TRY(pl->alloc(&h.t0, tcnt));
+  LRTEI_TRY(pl->alloc(&h.t1, tcnt));
+  LRTEI_TRY(pl->alloc(&h.t2, tcnt));
+  LRTEI_TRY(pl->alloc(&h.s0, scnt));
+  LRTEI_TRY(pl->alloc(&h.s1, scnt));
+  LRTEI_TRY(pl->alloc(&h.s1h, scnt));
+  LRTEI_TRY(pl->alloc(&h.s2, scnt));
+  LRTEI_TRY(pl->alloc(&h.te, 3ULL * h.P * h.nrows));
+  LRTEI_TRY(pl->alloc(&h.se, 3ULL * h.nrows));
+  LRTEI_TRY(pl->alloc(&h.f, (size_t)h.nrows * h.P));
+  LRTEI_TRY(pl->alloc(&h.ra, (size_t)h.nrows));
+  LRTEI_TRY(pl->alloc(&h.eb, (size_t)h.nrows));
+  Scratch sc(st);
+  double *Ss, *T;
+  LRTEI_TRY(sc.get(&Ss, 3ULL * h.nrows * h.n));
+  LRTEI_TRY(sc.get(&T, 3ULL * h.P * h.nrows * h.n));
+  {
+    ProfScope ps("hadamard_prep", st);
+    launch_had_prepare(h, pl->d_S, pl->d_C, pl->d_w, pl->omega / sqrt(kPi), pl->t.row_c, Ss, T, st);
+  }
+  pl->have_had = true;
+  return finish_launch("tensor-core Hadamard operands");
 }
 
 // Rows [r0, r1) of B_u (full width npair) into out (ld), prefactor included.
@@ -1129,7 +1174,14 @@ lrtei_status bu_rows(lrtei_plan* pl, int form, int64_t r0, int64_t r1, double* o
   const int n = pl->n, P = pl->P;
   const int64_t npair = pl->t.npair, n3 = (int64_t)n * n * n, nr = r1 - r0;
   if (nr <= 0) return LRTEI_OK;
-  if (is_split(pl)) return bu_rows_tc(pl, r0, r1, out, ld, st);
+  if (is_split(pl)) {
+    if (form == LRTEI_FORM_HADAMARD) {
+      LRTEI_TRY(ensure_had(pl, st));
+      LRTEI_TRY(had_tc_rows(pl->had, r0, r1, out, ld, pl->d_status, st));
+      return finish_launch("tensor-core Hadamard form");
+    }
+    return bu_rows_tc(pl, r0, r1, out, ld, st);
+  }
   if (form == LRTEI_FORM_HADAMARD) {
     LRTEI_TRY(ensure_T(pl, st));
     {
@@ -1328,9 +1380,9 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
     cudaError_t e = cudaPointerGetAttributes(&pa, d_B);
     if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(B)");
     if (pa.type == cudaMemoryTypeHost) {
-      // copy engines move B on the tensor-core path; the FP64 / FP32 expansion stores through the
-      // buffer's device alias
-      if (!pa.devicePointer && !is_split(plan)) {
+      // copy engines move B on the tensor-core factored path; the other paths' expansion stores
+      // through the buffer's device alias
+      if (!pa.devicePointer && !(is_split(plan) && choose_form(plan, form) == LRTEI_FORM_FACTORED)) {
         set_error("pinned host B is not mapped into the device address space");
         return LRTEI_ERR_ARG;
       }
@@ -1360,7 +1412,7 @@ lrtei_status lrtei_assemble_B(lrtei_plan* plan, lrtei_form form, double* d_B, in
     }
     return finish_launch("expand_B");
   }
-  if (hB && is_split(plan)) return assemble_B_host_banded(plan, hB, ld, st);
+  if (hB && is_split(plan) && f == LRTEI_FORM_FACTORED) return assemble_B_host_banded(plan, hB, ld, st);
   // process B_u in row blocks of at most ~1 GiB
   int64_t rb = std::max<int64_t>(1, (int64_t)((1ULL << 30) / (sizeof(double) * (size_t)npair)));
   if (f == LRTEI_FORM_FACTORED) {

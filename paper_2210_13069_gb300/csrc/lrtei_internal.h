@@ -131,6 +131,28 @@ void launch_gather_moments(int64_t count, int n, const int* d_key, const double*
 // ---------------------------------------------------------------- Hadamard form (FP64)
 // T[d][p][row][b] = sum_a S[d][row][a] C[d][p][a][b]
 void launch_tmat(int64_t nrows, int n, int P, const double* d_S, const double* d_C, double* d_T, cudaStream_t st);
+
+// Operands of the tensor-core Hadamard form (k_tc_hadamard.cu), for plans whose unique pairs hold
+// one primitive pair each: slices of T_{d,p} = S'_d A_d^(p) (A operand, rows [d][p][row]) and of
+// S'_d (B operand, rows [d][row]), S'_x carrying the rows' contraction coefficients; per-row
+// exponents; node factors f[row][p] = (w/sqrt(pi)) w_p 2^(Ea_p - Ra) as FP32 pairs, Ra and Eb.
+struct HadOperands {
+  int64_t nrows = 0;
+  int n = 0, kpad = 0, P = 0;
+  uint16_t *t0 = nullptr, *t1 = nullptr, *t2 = nullptr;                 // [3 P nrows][kpad]
+  uint16_t *s0 = nullptr, *s1 = nullptr, *s1h = nullptr, *s2 = nullptr;  // [3 nrows][kpad]
+  int *te = nullptr, *se = nullptr;                                      // [3 P nrows], [3 nrows]
+  float2* f = nullptr;                                                   // [nrows][P]
+  int *ra = nullptr, *eb = nullptr;                                      // [nrows]
+};
+// Fill h from the plan's moments (S, [3][nrows][n]), coefficients and weights; d_Ss (3 nrows n)
+// and d_T (3 P nrows n) are FP64 scratch.
+void launch_had_prepare(const HadOperands& h, const double* d_S, const double* d_C, const double* d_w, double pref,
+                        const double* d_row_c, double* d_Ss, double* d_T, cudaStream_t st);
+// Rows [r0, r1) of B_u by the tensor-core Hadamard form: the whole upper triangle with mirrors
+// into out (ld) when [r0, r1) is every row, else rows r0.. of a band at out + (r - r0) ld.
+lrtei_status had_tc_rows(const HadOperands& h, int64_t r0, int64_t r1, double* d_out, int64_t ld, int* d_status,
+                         cudaStream_t st);
 // Entries by Algorithm 1 on unique pairs: out[e] = B_u(r_e, c_e), prefactor included.
 // Entries whose r or c is negative (an index outside the basis) come out as NaN; a non-finite
 // result of a valid entry latches kDevNonFinite into *d_status.
