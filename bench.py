@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-nb360", action="store_true")
+    ap.add_argument("--no-uncontracted", action="store_true")
     ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
     ap.add_argument("--kr-eps", type=float, default=1e-8,
                     help="Khatri-Rao compression threshold of the compressed-form leg (0: leg off)")
@@ -551,6 +552,11 @@ def run_ours(args, world, rank, local):
     if args.kr_eps > 0 and args.precision in ("split_f16", "split_f16_8", "bf16"):
         kr = run_kr(args, mol, B, world, have_fp64_B=fp64 is not None)
 
+    # ---- the same molecule with one primitive per shell: the tensor-core Hadamard form
+    unc = None
+    if not args.no_uncontracted and args.precision == "split_f16":
+        unc = run_uncontracted(args, B, world)
+
     # ---- the same step with the eight-product scheme (error about seven times smaller)
     split8 = None
     if args.precision == "split_f16" and not args.no_fp64:
@@ -654,7 +660,7 @@ def run_ours(args, world, rank, local):
                        "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
-            "jbuilds": jb, "kr_compressed": kr, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "jbuilds": jb, "kr_compressed": kr, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "uncontracted_hadamard_tc": unc, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)
@@ -662,6 +668,50 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_uncontracted(args, B, world):
+    """The workload's 12 atoms and shells with one primitive per shell (an uncontracted basis):
+    B by the tensor-core Hadamard form (Algorithm 1's per-node products T_{d,p} S_d^T on the tensor
+    cores, K = n) and by the tensor-core factored form; time per B and entries/s of each, and the
+    Hadamard kernel's rate in the method's own flops (6 P n per unique element of B_u)."""
+    import torch
+    from paper_2210_13069_gb300 import lrtei, synth
+    stream = torch.cuda.current_stream()
+    mol = synth.workload_spd(natoms=args.natoms, nprim=1)
+    nb2 = mol.nbf * mol.nbf
+    npair = mol.nbf * (mol.nbf + 1) // 2
+    pl = lrtei.Plan(mol, "split_f16")
+    out = {"workload": f"nb{mol.nbf}_spd_uncontracted", "n": mol.n, "P": mol.P}
+    for form in ("hadamard", "factored"):
+        for _ in range(2):
+            pl.assemble_B(form, out=B)
+        torch.cuda.synchronize()
+        lrtei.lrtei_profile_reset()
+        lrtei.lrtei_profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            pl.assemble_B(form, out=B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        k_ms, k_cnt = lrtei.lrtei_profile_get("tc_hadamard" if form == "hadamard" else "tc_gemm")
+        lrtei.lrtei_profile_enable(False)
+        lrtei.lrtei_profile_reset()
+        pl.status()
+        ms = e0.elapsed_time(e1) / reps
+        out[form] = {"ms_per_B": ms, "entries_per_s": whole_job_rate(float(nb2) * nb2, world, ms, device="cuda"),
+                     "kernel_ms_per_B": k_ms / reps, "kernel_launches_per_B": k_cnt / reps}
+    kh = out["hadamard"]["kernel_ms_per_B"]
+    alg = 6.0 * mol.P * mol.n * (npair * (npair + 1) / 2)
+    out["hadamard"]["alg_tflops"] = alg / (kh * 1e-3) / 1e12 if kh > 0 else None
+    out["speedup_vs_factored"] = out["factored"]["ms_per_B"] / out["hadamard"]["ms_per_B"]
+    pl.assemble_B("auto", out=B)
+    out["auto_form"] = {1: "hadamard", 2: "factored"}.get(pl.info["last_form"], "?")
+    pl.close()
+    return out
 
 
 def run_kr(args, mol, B, world, have_fp64_B=False):

@@ -69,9 +69,15 @@ typedef enum {
                             seven times smaller (1e-9 to 2e-8 measured) */
 } lrtei_precision;
 
-/* Which of the two equivalent forms of Theorem 1 assembles B. */
+/* Which of the two equivalent forms of Theorem 1 assembles B.  On the FP64 and FP32 paths both
+ * run on the CUDA cores.  With LRTEI_SPLIT_F16 the factored form runs on the tensor cores, and so
+ * does the Hadamard form when every unique pair holds one primitive pair (an uncontracted basis,
+ * n <= 64, no compression or adaptive boxes): per node and dimension the tile products
+ * T_{d,p} S_d^T (depth n) on the tensor cores, the product over dimensions and the node sum in
+ * pairs of FP32 numbers; elsewhere the tensor-core precisions take the factored form whatever
+ * `form` asks.  lrtei_plan_info_get reports the form the last assembly used (last_form). */
 typedef enum {
-  LRTEI_FORM_AUTO = 0,      /* cost model: Hadamard when 3 P Ibar^2 <= n^2, else factored */
+  LRTEI_FORM_AUTO = 0,      /* cost model: Hadamard when P Ibar^2 (6n + 3) <= 2 n^3, else factored */
   LRTEI_FORM_HADAMARD = 1,  /* entry-wise Hadamard form (Theorem 1 / Algorithm 1) */
   LRTEI_FORM_FACTORED = 2   /* Khatri-Rao factored form (eq. tensors) */
 } lrtei_form;

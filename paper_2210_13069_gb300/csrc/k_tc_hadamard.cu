@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* done = acce + NBUF;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* epi_flag = abort_flag + 1;  // [2] the poller's result for the epilogue warps
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int steps_per_tile = p.P * 3;  // (p, d) products per tile
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int y = (int)(((int64_t)d * p.P + pp) * p.nrows + I * BM);
           for (int ks = 0; ks < KS; ++ks, ++it) {
             const int s = (int)(it % STAGES);
-            if (!mbar_wait(&empty[s], ((it / STAGES) & 1u) ^ 1u, abort_flag, p.status, 32)) { stop = true; break; }
+            if (!mbar_wait(&empty[s], ((it / STAGES) & 1u) ^ 1u, abort_flag, p.status, 256)) { stop = true; break; }
             mbar_arrive_expect_tx(&full[s], A_STAGE);
             uint8_t* a = sA + (size_t)s * A_STAGE;
             tma_load_2d(&ta0, a + 0 * A_PLANE, &full[s], ks * BK, y);
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int q = 0; q < steps_per_tile && ok; ++q, ++cg) {
           const int d = q % 3;
           const int buf = (int)(cg % NBUF);
-          if (!mbar_wait(&acce[buf], ((cg / NBUF) & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          // the epilogue is the slower side: poll its drained buffers at a relaxed pace
+          if (!mbar_wait(&acce[buf], ((cg / NBUF) & 1u) ^ 1u, abort_flag, p.status, 128)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d0 = tmem_base + (uint32_t)(buf * 2 * BN);
           const uint32_t d1 = d0 + BN;
@@ -333,18 +335,23 @@ __global__ void __launch_bounds__(THREADS, 1)
       tile_of(p, item, I, J);
       const int64_t r = I * BM + quad * 32 + lane;  // this thread's row of B_u
       const bool rlive = r < p.nrows;
-      float ah[QC], al[QC];
+      // node sum as an FP32 pair (as, al): two-sum of the leading parts, the rest in the trailing one
+      float as[QC], al[QC];
 #pragma unroll
-      for (int j = 0; j < QC; ++j) ah[j] = al[j] = 0.f;
+      for (int j = 0; j < QC; ++j) as[j] = al[j] = 0.f;
+      float2 fnext = rlive ? p.f[r * p.P] : make_float2(0.f, 0.f);
       for (int pp = 0; pp < p.P && ok; ++pp) {
+        const float2 f = fnext;  // this node's factor; the next one is fetched while it is used
+        if (pp + 1 < p.P && rlive) fnext = p.f[r * p.P + pp + 1];
         float ph[QC], pl[QC];
 #pragma unroll
         for (int d = 0; d < 3; ++d, ++cg) {
           const int buf = (int)(cg % NBUF);
-          int got = 1;
-          if (lane == 0) got = mbar_wait(&accf[buf], (cg / NBUF) & 1u, abort_flag, p.status) ? 1 : 0;
-          got = __shfl_sync(0xffffffffu, got, 0);
-          if (!got) { ok = false; break; }
+          // one thread polls the buffer's barrier; the epilogue warps meet on a named barrier
+          if (ew == 0 && lane == 0)
+            epi_flag[cg & 1u] = mbar_wait(&accf[buf], (cg / NBUF) & 1u, abort_flag, p.status) ? 1 : 0;
+          asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI) : "memory");
+          if (!epi_flag[cg & 1u]) { ok = false; break; }
           tc_fence_after();
           const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 2 * BN + col0);
 #pragma unroll
@@ -355,11 +362,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const float gh = __uint_as_float(l0[j]);                   // exact integer sum
+              const float gh = __uint_as_float(l0[j]);                      // exact integer sum
               const float gl = __uint_as_float(l12[j]) * (1.0f / 2048.0f);  // exact scaling
               if (d == 0) {
-                ph[j0 + j] = gh;
-                pl[j0 + j] = gl;
+                // f g: f is a normalised pair, so its trailing part times gl (2^-33) is dropped
+                const float t = f.x * gh;
+                float e = fmaf(f.x, gh, -t);
+                e = fmaf(f.x, gl, e);
+                e = fmaf(f.y, gh, e);
+                ph[j0 + j] = t;
+                pl[j0 + j] = e;
               } else {
                 pmul(ph[j0 + j], pl[j0 + j], gh, gl, ph[j0 + j], pl[j0 + j]);
               }
@@ -370,19 +382,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (lane == 0) mbar_arrive(&acce[buf]);
         }
         if (!ok) break;
-        const float2 f = rlive ? p.f[r * p.P + pp] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < QC; ++j) {
-          // term = f * prod (f's trailing part times prod's trailing part is below 2^-32)
-          const float th = f.x * ph[j];
-          float tl = fmaf(f.x, ph[j], -th);
-          tl = fmaf(f.x, pl[j], tl);
-          tl = fmaf(f.y, ph[j], tl);
-          padd(ah[j], al[j], th, tl);
-        }
+        for (int j = 0; j < QC; ++j) padd(as[j], al[j], ph[j], pl[j]);
       }
-      if (!ok || *abort_flag) break;
-      // store: B_u(r, c) = 2^(Ra(r) + Eb(c) - 48) (ah + al); the mirror B_u(c, r) too
+      // every epilogue warp takes the same exits (the poller's flag), as the named barrier needs
+      if (!ok) break;
+      // store: B_u(r, c) = 2^(Ra(r) + Eb(c) - 48) (as + al); the mirror B_u(c, r) too
       if (rlive && r >= p.r0 && r < p.r1) {
         const int rk = p.ra[r] - 48;
         const int64_t c0 = J * BN + col0;
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int j = 0; j < QC; ++j) {
             const int64_t c = c0 + j;
             if (c >= p.nrows || c < r) continue;
-            const double v = fpair_ldexp(ah[j], al[j], rk + p.eb[c]);
+            const double v = fpair_ldexp(as[j], al[j], rk + p.eb[c]);
             p.out[r * p.ld + c] = v;
             if (c != r) p.out[c * p.ld + r] = v;
           }
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < QC; ++j) {
             const int64_t c = c0 + j;
-            if (c < p.nrows) orow[c] = fpair_ldexp(ah[j], al[j], rk + p.eb[c]);
+            if (c < p.nrows) orow[c] = fpair_ldexp(as[j], al[j], rk + p.eb[c]);
           }
         }
       }

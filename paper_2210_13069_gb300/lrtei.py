@@ -430,10 +430,15 @@ class Plan:
         else:
             self.plan = lrtei_plan_create_ex(self.basis, omega or mol.omega, n or mol.n, P or mol.P, mol.box_lo,
                                              mol.box_hi, PRECISIONS[precision], tau_screening, stream)
-        self.info = lrtei_plan_info_get(self.plan)
-        self.nbf = self.info["nbf"]
-        self.npair = self.info["npair"]
+        info = lrtei_plan_info_get(self.plan)
+        self.nbf = info["nbf"]
+        self.npair = info["npair"]
         self._torch = torch
+
+    @property
+    def info(self) -> dict:
+        """lrtei_plan_info_get, read at each access (last_form follows the last assembly)."""
+        return lrtei_plan_info_get(self.plan)
 
     def close(self):
         if getattr(self, "plan", None):
@@ -503,7 +508,6 @@ class Plan:
     def compress(self, eps: float, max_rank: int = 0, stream=None):
         """Khatri-Rao compression (eq. approxepsilon); returns (singular values, ranks R_d)."""
         sig, ranks = lrtei_plan_compress(self.plan, eps, max_rank, self.info["n"], stream)
-        self.info = lrtei_plan_info_get(self.plan)
         return sig, ranks
 
     def exchange(self, Q, out=None, stream=None):
