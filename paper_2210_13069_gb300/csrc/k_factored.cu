@@ -268,6 +268,32 @@ void launch_kron_apply(int n, int P, const double* d_C, const double* d_w, const
 }
 
 // One block per unique pair r = (mu, nu); writes full rows mu*N_b+nu and nu*N_b+mu.
+// The column walk of one B row: col = t, t + step, ... with (ka, la) = (col / N_b, col % N_b)
+// advanced by additions (no 64-bit division per element), the non-finite test on the bit pattern
+// and the scale applied only when it is not 1 (this device's FP64 rate would otherwise make the
+// expansion ALU-bound rather than bound by its 12 GB of traffic).
+struct ColWalk {
+  int ka, la, dka, dla, nbf;
+  __device__ ColWalk(int nbf_, int t, int step) : nbf(nbf_) {
+    ka = t / nbf;
+    la = t % nbf;
+    dka = step / nbf;
+    dla = step % nbf;
+  }
+  __device__ void next() {
+    ka += dka;
+    la += dla;
+    if (la >= nbf) {
+      la -= nbf;
+      ++ka;
+    }
+  }
+};
+
+__device__ __forceinline__ bool nonfinite_bits(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7FF) == 0x7FF;
+}
+
 __global__ void k_expand_B(int nbf, const double* __restrict__ Bu, int64_t ldu, double scale, double* __restrict__ B,
                            int64_t ldB, const int* __restrict__ pair_mu, const int* __restrict__ pair_nu, int* status) {
   const int64_t r = blockIdx.x;
@@ -275,12 +301,14 @@ __global__ void k_expand_B(int nbf, const double* __restrict__ Bu, int64_t ldu, 
   const double* src = Bu + (size_t)r * ldu;
   double* row1 = B + ((size_t)mu * nbf + nu) * ldB;
   double* row2 = B + ((size_t)nu * nbf + mu) * ldB;
-  const int64_t nc = (int64_t)nbf * nbf;
+  const int nc = nbf * nbf;
+  const bool scaled = scale != 1.0;
   bool bad = false;
-  for (int64_t col = threadIdx.x; col < nc; col += blockDim.x) {
-    const int ka = (int)(col / nbf), la = (int)(col % nbf);
-    const double v = scale * src[pair_idx(nbf, ka, la)];
-    bad |= !isfinite(v);
+  ColWalk w(nbf, threadIdx.x, blockDim.x);
+  for (int col = threadIdx.x; col < nc; col += blockDim.x, w.next()) {
+    double v = src[pair_idx(nbf, w.ka, w.la)];
+    if (scaled) v *= scale;
+    bad |= nonfinite_bits(v);
     row1[col] = v;
     if (mu != nu) row2[col] = v;
   }
@@ -300,11 +328,12 @@ __global__ void k_expand_B_rows(int nbf, const double* __restrict__ Bu, int64_t 
   const int a = (int)(R / nbf), b = (int)(R % nbf);
   const double* src = Bu + (size_t)pair_idx(nbf, a, b) * ldu;
   double* dst = out + (size_t)blockIdx.x * ldo;
-  const int64_t nc = (int64_t)nbf * nbf;
+  const int nc = nbf * nbf;
   bool bad = false;
-  for (int64_t col = threadIdx.x; col < nc; col += blockDim.x) {
-    const double v = src[pair_idx(nbf, (int)(col / nbf), (int)(col % nbf))];
-    bad |= !isfinite(v);
+  ColWalk w(nbf, threadIdx.x, blockDim.x);
+  for (int col = threadIdx.x; col < nc; col += blockDim.x, w.next()) {
+    const double v = src[pair_idx(nbf, w.ka, w.la)];
+    bad |= nonfinite_bits(v);
     dst[col] = v;
   }
   latch_nonfinite_warp(status, bad);
