@@ -607,6 +607,7 @@ def run_ours(args, world, rank, local):
                 torch.cuda.synchronize()
                 ts.append(a0.elapsed_time(a1))
             nb20[f"{prec}_ms_median"] = statistics.median(ts)
+            nb20[f"{prec}_form"] = {1: "hadamard", 2: "factored"}.get(p20.info["last_form"], "?")
             p20.close()
 
     # ---- the 360-function instance (24 atoms, omega = 0.33): full 129 600^2 B (134 GB) per step.
