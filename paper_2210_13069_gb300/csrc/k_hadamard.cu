@@ -1,8 +1,9 @@
 // k_hadamard.cu -- FP64 CUDA-core form of Theorem 1 / Algorithm 1 (entry-wise Hadamard form):
 //   B_u(r, c) = (w/sqrt(pi)) sum_p w_p sum_{j in r} sum_{j' in c} c_j c_j' prod_d (T_{d,p}(j,:) . S_d(j',:))
 // with T_{d,p} = S_d A_d^(p) computed once per plan.  The sum over the quadrature nodes is
-// Neumaier-compensated in FP64.  This is the FP64 CUDA-core form of the contraction; the tensor-core
-// path (k_tcgen05.cu) runs the Khatri-Rao factored form of the same B instead.
+// Neumaier-compensated in FP64.  This is the FP64 CUDA-core form of the contraction; on the tensor
+// cores the same B comes from the Khatri-Rao factored form (k_tcgen05.cu) or, for bases with one
+// primitive pair per unique pair, from the tensor-core Hadamard form (k_tc_hadamard.cu).
 #include "lrtei_internal.h"
 
 namespace lrtei {
