@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
     ap.add_argument("--kr-eps", type=float, default=1e-8,
                     help="Khatri-Rao compression threshold of the compressed-form leg (0: leg off)")
-    ap.add_argument("--profile-region", choices=["none", "main", "jbuild"], default="none",
+    ap.add_argument("--profile-region", choices=["none", "main", "jbuild", "kr", "uncontracted"], default="none",
                     help="bracket that leg's timed launches with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="oracle seconds per step of the reference arm (default: the run stays within ~2.5 min)")
@@ -693,10 +693,15 @@ def run_uncontracted(args, B, world):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         reps = 3
+        region = args.profile_region == "uncontracted"
+        if region:
+            torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(reps):
             pl.assemble_B(form, out=B)
         e1.record(stream)
+        if region:
+            torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         k_ms, k_cnt = lrtei.lrtei_profile_get("tc_hadamard" if form == "hadamard" else "tc_gemm")
         lrtei.lrtei_profile_enable(False)
@@ -740,10 +745,14 @@ def run_kr(args, mol, B, world, have_fp64_B=False):
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
     reps = 5
+    if args.profile_region == "kr":
+        torch.cuda.profiler.start()
     k0.record(stream)
     for _ in range(reps):
         pk.assemble_B(args.form, out=B)
     k1.record(stream)
+    if args.profile_region == "kr":
+        torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     g_ms, g_cnt = lrtei.lrtei_profile_get("tc_gemm")
     lrtei.lrtei_profile_enable(False)
