@@ -26,6 +26,8 @@
 //               FP64 stores of the tile and its mirror at the end
 // Every mbarrier wait is bounded, as in the GEMM: on expiry the CTA raises the device status word,
 // stops issuing work, waits (bounded) for what it issued, frees TMEM and exits.
+#include <stdlib.h>
+
 #include <algorithm>
 
 #include "lrtei_internal.h"
@@ -71,6 +73,8 @@ struct Params {
   double* out;
   int64_t ld;
   int* status;
+  long long test_stall;  // > 0 (tests only): the MMA thread first waits this many cycles on a barrier
+                         // that nothing completes, so that the bounded-wait failure path runs
 };
 
 // Item -> (row block, column block).  Symmetric: row block I walks column blocks J >= 2 I (the
@@ -191,7 +195,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* accf = bempty + 1;       // [NBUF] accumulator buffer ready
   uint64_t* acce = accf + NBUF;      // [NBUF] accumulator buffer drained
   uint64_t* done = acce + NBUF;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* never = done + 1;        // completed by nobody (the test stall waits on it)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* epi_flag = abort_flag + 1;  // [2] the poller's result for the epilogue warps
 
@@ -210,6 +215,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&acce[b], EPI);
     }
     mbar_init(done, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -278,6 +284,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t idesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
       uint32_t it = 0, cg = 0, tl = 0;
       bool ok = true;
+      // test hook: a wait that runs out (nothing arrives on `never`), then the abort path
+      if (p.test_stall > 0) ok = mbar_wait(never, 0u, abort_flag, p.status, 0, p.test_stall);
       for (int64_t item = blockIdx.x; item < p.ntiles && ok; item += gridDim.x, ++tl) {
         if (!mbar_wait(bfull, tl & 1u, abort_flag, p.status)) break;
         tc_fence_after();
@@ -574,6 +582,12 @@ lrtei_status had_tc_rows(const HadOperands& h, int64_t r0, int64_t r1, double* d
   p.out = d_out;
   p.ld = ld;
   p.status = d_status;
+  {
+    // LRTEI_TEST_STALL_CYCLES (tests only), as for the GEMM: every CTA's MMA thread first waits that
+    // many cycles on a barrier nothing completes, raises LRTEI_ERR_TIMEOUT and drains
+    const char* v = getenv("LRTEI_TEST_STALL_CYCLES");
+    p.test_stall = (v && *v) ? std::max(0LL, atoll(v)) : 0;
+  }
   ProfScope ps("tc_hadamard", st);
   return h.kpad == 32 ? launch_had_kernel<1>(h, p, st) : launch_had_kernel<2>(h, p, st);
 }

@@ -3,7 +3,7 @@
 - A bounded wait of the tensor-core GEMM that runs out: the test hook LRTEI_TEST_STALL_CYCLES
   makes every CTA's MMA thread wait on a barrier that nothing completes; the wait gives up, the
   kernel leaves through its bounded drain path, lrtei_plan_status reports LRTEI_ERR_TIMEOUT, and
-  the next call on the same plan is correct again.
+  the next call on the same plan is correct again.  The same for the tensor-core Hadamard kernel.
 - An index list with a basis-function index outside [0, N_b): the device check gives that entry
   NaN and reads nothing for it, the other entries are unchanged, and the plan reports
   LRTEI_ERR_ARG (both entry points).
@@ -51,6 +51,33 @@ def test_gemm_wait_that_runs_out_reports_timeout_then_recovers(lib):
     pl.status()
     err = np.linalg.norm(B - ref) / np.linalg.norm(ref)
     assert err <= 1e-7, err
+    pl.close()
+
+
+def test_hadamard_kernel_wait_that_runs_out_reports_timeout_then_recovers(lib):
+    """The same bounded-wait failure path in the tensor-core Hadamard kernel (uncontracted s
+    functions): its MMA thread waits on a barrier nothing completes, every role leaves through
+    its bounded drain, the plan reports LRTEI_ERR_TIMEOUT, and the next call is correct."""
+    import torch
+    m = synth.workload_small_s()
+    ref_plan = lib.Plan(m, "fp64")
+    ref = ref_plan.assemble_B("hadamard").cpu().numpy()
+    ref_plan.close()
+    pl = lib.Plan(m, "split_f16")
+    os.environ["LRTEI_TEST_STALL_CYCLES"] = "200000"
+    try:
+        pl.assemble_B("hadamard")
+        torch.cuda.synchronize()
+    finally:
+        del os.environ["LRTEI_TEST_STALL_CYCLES"]
+    with pytest.raises(lib.LrteiError) as ei:
+        pl.status()
+    assert ei.value.status == 4, ei.value
+    B = pl.assemble_B("hadamard").cpu().numpy()
+    pl.status()
+    assert pl.info["last_form"] == 1
+    err = np.linalg.norm(B - ref) / np.linalg.norm(ref)
+    assert err <= 2e-8, err
     pl.close()
 
 
