@@ -250,6 +250,22 @@ def cpu_oracle_rate(mol, budget_s: float, seed: int = 99):
     return total_entries / total_t, threads, f"{total_entries} random entries (mu,nu,ka,la) of B, Algorithm 1 per entry incl. their pair moments, {total_t:.1f} s"
 
 
+def cpu_oracle_jbuild_rate(mol, R: int = 32, seed: int = 4242):
+    """J-builds/s of the FP64 oracle's factored form (eq. coulapprox with the Kronecker mode
+    products of eq. ig1) on R densities in one call, all host cores; the moments are computed by
+    an untimed first call on one density, as the GPU leg's plan holds them too."""
+    import oracle
+    from paper_2210_13069_gb300 import synth
+    threads = os.cpu_count() or 1
+    o = oracle.Oracle.from_molecule(mol)
+    D = synth.random_densities(seed, mol.nbf, R)
+    o.jbuild_factored(D[:1], threads=threads)
+    t0 = time.perf_counter()
+    o.jbuild_factored(D, threads=threads)
+    dt = time.perf_counter() - t0
+    return R / dt, f"{R} densities through the oracle's factored J-build (moments precomputed), {dt:.1f} s"
+
+
 # ------------------------------------------------------------------ screening leg
 
 def run_screening(args, mol, B, tau=1e-10):
@@ -645,6 +661,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(mol, budget_s=15.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if not args.no_jbuild:
+            jr, jsample = cpu_oracle_jbuild_rate(mol)
+            cpu["jbuilds_per_s"] = jr
+            cpu["jbuild_sample"] = jsample
 
     if rank == 0:
         dtype = {"split_f16": "f16x3 (8+11+11-bit integer slices, fp32 acc)",
