@@ -196,9 +196,10 @@ def test_selector_meets_target_judged_by_the_oracle(lib, trained):
     assert np.mean(gains) > 1.0
 
 
-def test_selector_on_a_600_function_molecule(lib, trained):
-    """A 40-atom, 600-function s/p/d molecule (cube side 12 (40/12)^(1/3) bohr, omega = 0.3), eight
-    densities, target 1e-6: the factored J-build at the selected (n, P) and at the fixed (32, 48),
+@pytest.mark.parametrize("seed,omega", [(5000, 0.3), (5001, 0.8)])
+def test_selector_on_a_600_function_molecule(lib, trained, seed, omega):
+    """A 40-atom, 600-function s/p/d molecule (cube side 12 (40/12)^(1/3) bohr, omega = 0.3 or 0.8),
+    eight densities, target 1e-6: the factored J-build at the selected (n, P) and at the fixed (32, 48),
     both split-F16 on the tensor cores, against an FP64 J-build at a larger (n, P).  F_u does not
     fit in device memory at these orders, so the J-builds stream it in blocks of unique pairs.
     The selected (n, P) meets the target."""
@@ -207,7 +208,7 @@ def test_selector_on_a_600_function_molecule(lib, trained):
     from paper_2210_13069_gb300 import selector as S, synth
     sel, _, _ = trained
     target, R = 1e-6, 8
-    m = synth.random_molecule(5000, natoms=40, cube=12.0 * (40 / 12) ** (1 / 3), omega=0.3, n=32, P=48,
+    m = synth.random_molecule(seed, natoms=40, cube=12.0 * (40 / 12) ** (1 / 3), omega=omega, n=32, P=48,
                               name="nb600_spd")
     assert m.nbf == 600
     amin, amax, lmax = S.molecule_features(m)
@@ -238,7 +239,7 @@ def test_selector_on_a_600_function_molecule(lib, trained):
     J_ref, t_ref = jbuild("fp64", n_ref, P_ref)
     e_sel = float(np.linalg.norm(J_sel - J_ref) / np.linalg.norm(J_ref))
     e_fix = float(np.linalg.norm(J_fix - J_ref) / np.linalg.norm(J_ref))
-    print(f"selector N_b=600 (omega 0.3, box half-width {half:.1f}): selected (n, P) = ({n_sel}, {P_sel}): error "
+    print(f"selector N_b=600 (omega {omega}, box half-width {half:.1f}): selected (n, P) = ({n_sel}, {P_sel}): error "
           f"{e_sel:.2e}, plan + J-build {t_sel:.1f} s; fixed (32, 48): error {e_fix:.2e}, {t_fix:.1f} s; "
           f"reference FP64 ({n_ref}, {P_ref}) {t_ref:.1f} s")
     assert e_sel <= target
