@@ -1048,12 +1048,19 @@ static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const 
   const Config* cands = plain    ? (BN == 64 ? kPlainCfg64 : kPlainCfg32)
                         : A.eight ? (BN == 64 ? kSplit8Cfg64 : kSplit8Cfg32)
                                   : (BN == 128 ? kSplitCfg128 : BN == 64 ? kSplitCfg64 : kSplitCfg32);
-  const int ncand = 2;
+  // A third candidate for the non-symmetric six-product products with 128-column tiles: the CTA
+  // pair (cta_group::2, 256 x 128 tiles, each SM loading half of B), bit-identical results.
+  const bool pair_ok = !plain && !A.eight && BN == 128 && B.s1h && !p.symmetric && splits == 1 &&
+                       p.M < (1LL << 31);
+  const int ncand = pair_ok ? 3 : 2;
+  auto launch_cand = [&](int i) {
+    return i == 2 ? launch_tc_2sm<64, 2>(A, B, p, st) : launch_cfg(A, B, p, splits, plain, cands[i], st);
+  };
   const char* force = getenv("LRTEI_TC_CONFIG");
   if (force && *force) {
     const int i = atoi(force);
     ProfScope ps("tc_gemm", st);
-    return launch_cfg(A, B, p, splits, plain, cands[(i < 0 || i >= ncand) ? 0 : i], st);
+    return launch_cand((i < 0 || i >= ncand) ? 0 : i);
   }
   const auto key = std::make_tuple(p.M, p.N, A.kpad, splits, (int)plain + 2 * (int)A.eight,
                                    p.symmetric ? (int)(1 + p.blk0) : 0, p.transpose_out);
@@ -1072,7 +1079,7 @@ static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const 
     for (int round = 0; round < 2; ++round)
       for (int i = 0; i < ncand; ++i) {
         cudaEventRecord(e0, st);
-        lrtei_status s = launch_cfg(A, B, p, splits, plain, cands[i], st);
+        lrtei_status s = launch_cand(i);
         if (s != LRTEI_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
         cudaEventRecord(e1, st);
         cudaError_t e = cudaEventSynchronize(e1);
@@ -1089,7 +1096,7 @@ static lrtei_status run_tuned(const SplitMatrix& A, const SplitMatrix& B, const 
   }
   if (choice < 0) choice = 0;
   ProfScope ps("tc_gemm", st);
-  return launch_cfg(A, B, p, splits, plain, cands[choice], st);
+  return launch_cand(choice);
 }
 }  // namespace tc
 
