@@ -433,7 +433,8 @@ def run_ours(args, world, rank, local):
         if args.precision == "split_f16":
             # operand bytes the tensor-core GEMMs load per step (128 x 128 tiles, seven 16-bit planes
             # of 128 rows per 64-deep K step), per SM and clock, against the per-SM TMA delivery
-            # measured with the MMAs switched off (65-68 B/clk/SM, independent of the SM count)
+            # measured with the MMAs switched off (65-68 B/clk/SM, independent of the SM count); an
+            # upper bound when the tuner keeps the CTA-pair kernel for G (5/7 of these bytes there)
             tm = (npair + 127) // 128
             kpad = (n3 + 255) // 256 * 256
             tiles = tm * ((n3 + 127) // 128) + tm * (tm + 1) // 2
@@ -441,7 +442,8 @@ def run_ours(args, world, rank, local):
             mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
             bpc = loaded * args.steps / (tot_ms / 1e3) / 152 / (mhz * 1e6)
             roofline["operand_delivery"] = {"achieved_B_per_clk_per_sm": bpc, "ceiling_B_per_clk_per_sm": 66.0,
-                                            "frac": bpc / 66.0, "bytes_per_step": loaded}
+                                            "frac": bpc / 66.0, "bytes_per_step": loaded,
+                                            "assumes": "one-SM 128 x 128 tiles for both products"}
 
     # ---- J-builds/s (32 densities), same plan
     jb = None
