@@ -3,8 +3,9 @@
 // primitive-pair table (Proposition 1) and the 1D moment matrices S_d (eq. defV).
 //
 // All of this is FP64 on the device.  The moment integrals are computed by an 8-panel (16 above
-// n = 32), 32-point Gauss-Legendre rule over the window |x - P| <= 9/sqrt(p) of each primitive-pair
-// Gaussian, clipped to the box: one warp per (row, dimension), one lane per quadrature point.
+// n = 32), 16-point Gauss-Legendre rule over the window |x - P| <= 9/sqrt(p) of each primitive-pair
+// Gaussian, clipped to the box: one warp per (row, dimension), two panels per step (one per
+// half-warp), one lane per quadrature point.
 #include <math.h>
 
 #include <algorithm>
@@ -276,8 +277,9 @@ void launch_pair_rows(const PairTable& t, const int* d_bf_shell, const int* d_bf
 
 // ------------------------------------------------------------------ moments ----
 // S_d(row, m) = int_{lo_d}^{hi_d} (x-A)^i (x-B)^k K_AB exp(-p (x-P)^2) T_m((x - c_d)/h_d) dx.
-// One warp per (row, d); lane q holds quadrature point q of every panel and accumulates
-// f(x_q) w_q T_m(u_q) for all m in registers; a shared-memory transpose then sums over lanes.
+// One warp per (row, d); lane q holds quadrature point q % 16 of every other panel and
+// accumulates f(x_q) w_q T_m(u_q) for all m in registers; a shared-memory transpose then sums
+// over lanes.
 // Items are (d, row) = dr / nrows, dr % nrows with dr = rep[item] (or dr = item without rep;
 // rep[item] < 0 marks an unused item); item's moments go to S[item * n + m].
 template <int NM>
@@ -308,12 +310,14 @@ __global__ void __launch_bounds__(128) k_moments(int64_t nrows, int n, const dou
     const double reach = 9.0 / sqrt(p);
     const double wl = fmax(lo, Pc - reach), wh = fmin(hi, Pc + reach);
     if (wh > wl) {
-      // T_{n-1} oscillates across the box: above n = 32 the window takes twice the panels (the
-      // 32-point rule on a panel is exact to degree 63 of the polynomial factor times T_m)
+      // T_{n-1} oscillates across the box: above n = 32 the window takes twice the panels.  The
+      // 16-point rule (exact to degree 31 on a panel) resolves each panel's share of the
+      // Gaussian times the polynomial factor times T_m to rounding: half-warps take alternate
+      // panels, lane & 15 the point.
       const int npan = n <= 32 ? kMomentPanels : 2 * kMomentPanels;
       const double hp = (wh - wl) / npan;
-      const double zq = gz[lane], wq = gw[lane];
-      for (int pan = 0; pan < npan; ++pan) {
+      const double zq = gz[lane & 15], wq = gw[lane & 15];
+      for (int pan = lane >> 4; pan < npan; pan += 2) {
         const double mid = wl + (pan + 0.5) * hp;
         const double x = mid + 0.5 * hp * zq;
         const double dx = x - Pc;

@@ -15,7 +15,7 @@ namespace lrtei {
 constexpr int kMaxN = 64;        // Chebyshev nodes per dimension
 constexpr int kMaxP = 128;       // Gauss-Legendre nodes over [0, omega]
 constexpr int kMomentPanels = 8; // panels of the device moment quadrature (n <= 32; 16 above)
-constexpr int kMomentPts = 32;   // Gauss-Legendre points per panel (one per lane)
+constexpr int kMomentPts = 16;   // Gauss-Legendre points per panel (two panels per warp step)
 
 // Device-side status word (latched by kernels, read by lrtei_plan_status).
 enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevNonFinite = 2, kDevBadIndex = 3 };
