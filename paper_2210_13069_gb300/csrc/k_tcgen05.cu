@@ -543,8 +543,9 @@ static lrtei_status launch_tc(const SplitMatrix& A, const SplitMatrix& B, const 
 // the same MMA work per SM.  Both CTAs' TMA loads complete on the leader's "full" barrier; the
 // leader's MMA commits arrive on both CTAs' "empty" and "accumulator ready" barriers (multicast);
 // both CTAs' epilogue warps arrive on the leader's "accumulator drained" barrier.  Six products,
-// 128 x 128 tiles per CTA, 64-deep stages, two stages; no symmetric walk.  Every wait is bounded
-// as in k_tc_gemm.
+// 128 x 128 tiles per CTA, two 64-deep or five 32-deep stages; the symmetric product walks pairs
+// of block rows.  The tuner times it beside the one-SM configurations (run_tuned).  Every wait is
+// bounded as in k_tc_gemm.
 namespace pair2 {
 constexpr int BN = 128;      // columns of the pair's tile (N of the MMA)
 constexpr int HB = BN / 2;   // B rows each CTA loads
@@ -1191,9 +1192,9 @@ static lrtei_status tc_gemm_impl(const SplitMatrix& A, const SplitMatrix& B, int
                       (!symmetric_upper || (two[0] == '2' && p.blk0 % 2 == 0)) && p.M < (1LL << 31);
   if (two_ok) {
     ProfScope ps("tc_gemm", st);
-    // stage shape: LRTEI_TC_2SM_BK=64 selects two 64-deep stages, else five 32-deep ones
+    // stage shape: LRTEI_TC_2SM_BK=32 selects five 32-deep stages, else two 64-deep ones
     const char* bk = getenv("LRTEI_TC_2SM_BK");
-    s = (bk && atoi(bk) == 64) ? tc::launch_tc_2sm<64, 2>(A, B, p, st) : tc::launch_tc_2sm<32, 5>(A, B, p, st);
+    s = (bk && atoi(bk) == 32) ? tc::launch_tc_2sm<32, 5>(A, B, p, st) : tc::launch_tc_2sm<64, 2>(A, B, p, st);
   } else {
     s = tc::run_tuned(A, B, p, splits, BN, plain, st);
   }

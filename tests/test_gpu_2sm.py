@@ -1,7 +1,8 @@
 """The 2-SM tensor-core GEMM (cta_group::2: a CTA pair computes 256 x 128 tiles, each SM loading
 half of B), against the one-SM kernel and the oracle.  LRTEI_TC_2SM=1 selects it for the
 non-symmetric six-product GEMMs with 128-column tiles (G = F_u K), =2 for the symmetric B_u = G F_u^T
-too; LRTEI_TC_2SM_BK=64 gives it two 64-deep operand stages instead of five 32-deep ones."""
+too; LRTEI_TC_2SM_BK=32 gives it five 32-deep operand stages instead of two 64-deep ones.  Without
+the variable the tuner times the pair kernel beside the one-SM configurations."""
 import numpy as np
 import pytest
 
@@ -49,10 +50,12 @@ def test_two_sm_assembly_matches_oracle_and_one_sm(lib, maker, flag, bk, monkeyp
     rows = [0, nbf + 3, (nbf // 2) * nbf + nbf // 3, nbf * nbf - 1]
     ref = o.B_rows(rows)
     monkeypatch.delenv("LRTEI_TC_2SM", raising=False)
+    monkeypatch.setenv("LRTEI_TC_CONFIG", "0")  # the one-SM kernel, not the tuner's choice
     p1 = lib.Plan(m, "split_f16")
     B1 = p1.assemble_B().cpu().numpy()
     p1.status()
     p1.close()
+    monkeypatch.delenv("LRTEI_TC_CONFIG")
     monkeypatch.setenv("LRTEI_TC_2SM", flag)
     monkeypatch.setenv("LRTEI_TC_2SM_BK", bk)
     p2 = lib.Plan(m, "split_f16")
@@ -81,6 +84,10 @@ def test_two_sm_full_size_180(lib, monkeypatch):
     for flag, bk in runs:
         monkeypatch.setenv("LRTEI_TC_2SM", flag)
         monkeypatch.setenv("LRTEI_TC_2SM_BK", bk)
+        if flag == "0":
+            monkeypatch.setenv("LRTEI_TC_CONFIG", "0")  # the one-SM kernel, not the tuner's choice
+        else:
+            monkeypatch.delenv("LRTEI_TC_CONFIG", raising=False)
         pl = lib.Plan(m, "split_f16")
         B = pl.assemble_B()
         pl.assemble_B(out=B)

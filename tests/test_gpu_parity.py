@@ -375,11 +375,12 @@ def test_split_f16_full_size_180(lib):
     assert err <= 1e-7
 
 
-@pytest.mark.parametrize("cfg", ["0", "1"])
+@pytest.mark.parametrize("cfg", ["0", "1", "2"])
 def test_split_f16_each_tile_config(lib, cfg, monkeypatch):
     """Every kernel configuration the tuner may pick (64- and 32-deep K stages; 128x128 tiles
-    for B, 128x64 and 128x32 tiles for J-builds of 40 and 7 densities) gives the same accuracy
-    on B and J; the 45-function instance leaves ragged tails in every tile shape."""
+    for B, 128x64 and 128x32 tiles for J-builds of 40 and 7 densities; the CTA-pair kernel for the
+    non-symmetric G product, configuration 2, which the J-build shapes do not have) gives the same
+    accuracy on B and J; the 45-function instance leaves ragged tails in every tile shape."""
     import torch
     monkeypatch.setenv("LRTEI_TC_CONFIG", cfg)
     m = mol_ragged()
