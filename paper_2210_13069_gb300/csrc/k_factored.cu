@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "lrtei_internal.h"
+#include "tc_common.h"
 
 namespace lrtei {
 
@@ -143,6 +144,90 @@ __device__ __forceinline__ void dot2_step(Pair32 x, Pair32 z, float& sum, float&
   const float d = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
   sum = t;
   err = __fadd_rn(err, __fadd_rn(d, pe));
+}
+
+// F_u for the tensor-core precisions, whose F_u only feeds 30-bit slices: the same staged walk
+// with every product and the sum over the pair's rows j in pairs of FP32 numbers (the moments
+// converted to pairs once, y = S_y S_z by TwoProd, the sum over j by the compensated dot product
+// below), stored as FP64 from the pair by integer arithmetic: ~2^-44 of each term's size, against
+// FP64's 2^-53, at this part's FP32 rate instead of its FP64 rate.
+__global__ void k_S_pairs(int64_t count, const double* __restrict__ S, float2* __restrict__ Sp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const Pair32 q = to_pair(S[i]);
+    Sp[i] = make_float2(q.hi, q.lo);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_build_F_pairs(int n, int64_t nrows, const int64_t* __restrict__ pair_row,
+                                                       const double* __restrict__ row_c, const double* __restrict__ S,
+                                                       const float2* __restrict__ Sp, int64_t r0,
+                                                       double* __restrict__ F, int64_t ldF) {
+  extern __shared__ float2 Xp[];  // [rows of the pair][n8]: c_j S_x(j, m1) as pairs
+  const int64_t r = r0 + blockIdx.x;
+  const int64_t j0 = pair_row[r];
+  const int I = (int)(pair_row[r + 1] - j0);
+  const int n8 = (n + 7) / 8 * 8, nn = n * n;
+  const float2* Sy = Sp + (size_t)nrows * n;
+  const float2* Sz = Sp + 2 * (size_t)nrows * n;
+  for (int e = threadIdx.x; e < I * n8; e += blockDim.x) {
+    const int j = e / n8, m1 = e % n8;
+    const Pair32 q = to_pair(m1 < n ? row_c[j0 + j] * S[(size_t)(j0 + j) * n + m1] : 0.0);
+    Xp[e] = make_float2(q.hi, q.lo);
+  }
+  __syncthreads();
+  double* out = F + (size_t)blockIdx.x * ldF;
+  const int items = nn * (n8 / 8);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int q = it % nn, g = it / nn;
+    const int m2 = q / n, m3 = q % n;
+    float sum[8], err[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sum[i] = err[i] = 0.f;
+    for (int j = 0; j < I; ++j) {
+      const float2 a = Sy[(size_t)(j0 + j) * n + m2], b = Sz[(size_t)(j0 + j) * n + m3];
+      const float yh = __fmul_rn(a.x, b.x);
+      float yl = fmaf(a.x, b.x, -yh);  // TwoProd
+      yl = fmaf(a.x, b.y, fmaf(a.y, b.x, yl));
+      const Pair32 y{yh, yl};
+      const float2* xr = Xp + j * n8 + g * 8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float2 x = xr[i];
+        dot2_step(Pair32{x.x, x.y}, y, sum[i], err[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (g * 8 + i < n) out[(size_t)(g * 8 + i) * nn + q] = tc::fpair_ldexp(sum[i], err[i], 0);
+  }
+}
+
+void launch_build_F_pairs(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, double* d_F,
+                          int64_t ldF, cudaStream_t st) {
+  const size_t smem = sizeof(float2) * (size_t)t.maxI * ((n + 7) / 8 * 8);
+  if (t.maxI <= 0 || smem > 48 * 1024) {  // very long pair blocks: the FP64 build
+    launch_build_F<double>(t, n, d_S, r0, r1, d_F, ldF, st);
+    return;
+  }
+  const int64_t count = 3 * t.nrows * n;
+  float2* Sp = nullptr;
+  if (scratch_alloc((void**)&Sp, sizeof(float2) * (size_t)std::max<int64_t>(count, 1), st) != cudaSuccess) {
+    cudaGetLastError();
+    launch_build_F<double>(t, n, d_S, r0, r1, d_F, ldF, st);  // no scratch: the FP64 build
+    return;
+  }
+  count_launch();
+  k_S_pairs<<<(unsigned)std::min<int64_t>((count + 255) / 256, 152 * 32), 256, 0, st>>>(count, d_S, Sp);
+  int64_t nr = r1 - r0;
+  while (nr > 0) {
+    const int64_t chunk = nr > (1LL << 30) ? (1LL << 30) : nr;
+    count_launch();
+    k_build_F_pairs<<<(unsigned)chunk, 256, smem, st>>>(n, t.nrows, t.pair_row, t.row_c, d_S, Sp, r0, d_F, ldF);
+    r0 += chunk;
+    d_F += chunk * ldF;
+    nr -= chunk;
+  }
+  cudaFreeAsync(Sp, st);
 }
 
 __global__ void __launch_bounds__(512, 1) k_build_K_tiled(int n, int P, const double* __restrict__ C,

@@ -116,65 +116,6 @@ __device__ __forceinline__ void padd(float& ah, float& al, float bh, float bl) {
   al = al + (bl + err);
 }
 
-// An FP32 number as m 2^e, |m| < 2^24.
-__device__ __forceinline__ int64_t f32_int(float f, int& e) {
-  const uint32_t b = __float_as_uint(f);
-  const int E = (int)((b >> 23) & 0xFFu);
-  int64_t m = (int64_t)(b & 0x7FFFFFu);
-  if (E) m |= 0x800000;
-  e = (E ? E : 1) - 150;
-  return (b >> 31) ? -m : m;
-}
-
-// (hi + lo) 2^k in FP64, from integer arithmetic (this device's FP64 rate would make an FP64
-// store path a visible share of the kernel): hi + lo = X 2^q exactly with |X| < 2^63 (lo dropped
-// when more than 2^38 below hi), then X 2^(q+k) rounded to 53 bits (half up on the magnitude).
-// Results below the normal range flush to 0.
-__device__ __forceinline__ double fpair_ldexp(float hi, float lo, int k) {
-  int eh, el;
-  int64_t mh = f32_int(hi, eh), ml = f32_int(lo, el);
-  if (mh == 0) {
-    mh = ml;
-    eh = el;
-    ml = 0;
-  }
-  if (mh == 0) return 0.0;
-  int64_t X;
-  int q;
-  if (ml == 0 || eh - el > 38) {
-    X = mh;
-    q = eh;
-  } else if (el - eh > 38) {
-    X = ml;
-    q = el;
-  } else if (el >= eh) {
-    X = mh + (ml << (el - eh));
-    q = eh;
-  } else {
-    X = (mh << (eh - el)) + ml;
-    q = el;
-  }
-  if (X == 0) return 0.0;
-  const uint64_t a = (uint64_t)(X < 0 ? -X : X);
-  const int top = 63 - __clzll((long long)a);  // leading bit
-  uint64_t mant;
-  int E = top + q + k + 1023;
-  if (top > 52) {
-    const int sh = top - 52;
-    mant = (a + (1ULL << (sh - 1))) >> sh;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++E;
-    }
-  } else {
-    mant = a << (52 - top);
-  }
-  if (E <= 0) return 0.0;
-  if (E > 2046) E = 2046;
-  const uint64_t bits = ((uint64_t)(X < 0) << 63) | ((uint64_t)E << 52) | (mant & ((1ULL << 52) - 1));
-  return __longlong_as_double((long long)bits);
-}
-
 // ------------------------------------------------------------------ the kernel
 template <int KS>
 __global__ void __launch_bounds__(THREADS, 1)

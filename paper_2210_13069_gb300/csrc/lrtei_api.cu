@@ -626,13 +626,17 @@ lrtei_status ensure_T(lrtei_plan* pl, cudaStream_t st) {
   return finish_launch("tmat");
 }
 
+bool is_split(const lrtei_plan* pl);
+
 lrtei_status ensure_F64(lrtei_plan* pl, cudaStream_t st) {
   if (pl->d_F) return LRTEI_OK;
   const int64_t n3 = (int64_t)pl->n * pl->n * pl->n;
   LRTEI_TRY(pl->alloc(&pl->d_F, (size_t)pl->t.npair * n3));
   {
     ProfScope ps("build_F", st);
-    launch_build_F<double>(pl->t, pl->n, pl->d_S, 0, pl->t.npair, pl->d_F, n3, st);
+    // the tensor-core precisions read F_u through 30-bit slices: FP32 pairs (~2^-44) suffice
+    if (is_split(pl)) launch_build_F_pairs(pl->t, pl->n, pl->d_S, 0, pl->t.npair, pl->d_F, n3, st);
+    else launch_build_F<double>(pl->t, pl->n, pl->d_S, 0, pl->t.npair, pl->d_F, n3, st);
   }
   return finish_launch("build_F");
 }

@@ -172,6 +172,10 @@ void launch_idx4_to_pairs(int nbf, const int32_t* d_idx4, int64_t count, int64_t
 template <typename T>
 void launch_build_F(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, T* d_F, int64_t ldF,
                     cudaStream_t st);
+// The same F_u in pairs of FP32 numbers, stored as FP64 (~2^-44 relative per term): for the
+// tensor-core precisions, whose F_u only feeds 30-bit slices.
+void launch_build_F_pairs(const PairTable& t, int n, const double* d_S, int64_t r0, int64_t r1, double* d_F,
+                          int64_t ldF, cudaStream_t st);
 // Dense K = sum_p w_p C_x^p (x) C_y^p (x) C_z^p  (n^3 x n^3), FP64.
 cudaError_t launch_build_K(int n, int P, const double* d_C, const double* d_w, double scale, double* d_K,
                            cudaStream_t st);

@@ -193,6 +193,72 @@ __device__ __forceinline__ void slice_store(double x, int e, bool live, int nsli
   if (s1h) s1h[o] = f16_bits(b * (1.0f / 2048.0f));
 }
 
+// ------------------------------------------------------------------ FP32 pairs to FP64
+// An FP32 number as m 2^e, |m| < 2^24.
+__device__ __forceinline__ int64_t f32_int(float f, int& e) {
+  const uint32_t b = __float_as_uint(f);
+  const int E = (int)((b >> 23) & 0xFFu);
+  int64_t m = (int64_t)(b & 0x7FFFFFu);
+  if (E) m |= 0x800000;
+  e = (E ? E : 1) - 150;
+  return (b >> 31) ? -m : m;
+}
+
+// (hi + lo) 2^k in FP64 from integer arithmetic (this device's FP64 rate would make FP64
+// conversions a visible share of the kernels that store pairs): hi + lo = X 2^q with |X| < 2^63,
+// exact when the two exponents lie within 38 bits, else the smaller part rounded at 2^-62 of the
+// larger; then X 2^(q+k) rounded to 53 bits (half up on the magnitude).  Results below the normal
+// range flush to 0.
+__device__ __forceinline__ double fpair_ldexp(float hi, float lo, int k) {
+  int eb, es;
+  int64_t mb = f32_int(hi, eb), ms = f32_int(lo, es);
+  if (mb == 0 || (ms != 0 && es > eb)) {  // (mb, eb): the part with the larger exponent
+    const int64_t tm = mb;
+    mb = ms;
+    ms = tm;
+    const int te = eb;
+    eb = es;
+    es = te;
+  }
+  if (mb == 0) return 0.0;
+  int64_t X;
+  int q;
+  if (ms == 0) {
+    X = mb;
+    q = eb;
+  } else if (eb - es <= 38) {
+    X = (mb << (eb - es)) + ms;
+    q = es;
+  } else {
+    const int sh = eb - es - 38;
+    X = mb << 38;
+    if (sh < 62) {
+      const int64_t half = 1LL << (sh - 1);
+      X += ms >= 0 ? ((ms + half) >> sh) : -((-ms + half) >> sh);
+    }
+    q = es + sh;
+  }
+  if (X == 0) return 0.0;
+  const uint64_t a = (uint64_t)(X < 0 ? -X : X);
+  const int top = 63 - __clzll((long long)a);  // leading bit
+  uint64_t mant;
+  int E = top + q + k + 1023;
+  if (top > 52) {
+    const int sh = top - 52;
+    mant = (a + (1ULL << (sh - 1))) >> sh;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++E;
+    }
+  } else {
+    mant = a << (52 - top);
+  }
+  if (E <= 0) return 0.0;
+  if (E > 2046) E = 2046;
+  const uint64_t bits = ((uint64_t)(X < 0) << 63) | ((uint64_t)E << 52) | (mant & ((1ULL << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
 // ------------------------------------------------------------------ host: tensor maps
 inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
