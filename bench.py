@@ -575,7 +575,7 @@ def run_ours(args, world, rank, local):
     if not args.no_uncontracted and args.precision == "split_f16":
         unc = run_uncontracted(args, B, world)
 
-    # ---- the same step with the eight-product scheme (error about seven times smaller)
+    # ---- the same step with the eight-product scheme (error several times smaller)
     split8 = None
     if args.precision == "split_f16" and not args.no_fp64:
         p8 = lrtei.Plan(mol, "split_f16_8")
@@ -628,15 +628,15 @@ def run_ours(args, world, rank, local):
             nb20[f"{prec}_form"] = {1: "hadamard", 2: "factored"}.get(p20.info["last_form"], "?")
             p20.close()
 
-    # ---- the 360-function instance (24 atoms, omega = 0.33): full 129 600^2 B (134 GB) per step.
-    # Six products measured 1.06e-7 on sampled rows of it: it runs the eight-product scheme.
+    # ---- the 360-function instance (24 atoms, omega = 0.33): full 129 600^2 B (134 GB) per step,
+    # in the bench's precision (six products: 5e-8 on its sampled rows, tests/test_gpu_nb360.py).
     nb360 = None
     if not args.no_nb360 and args.natoms == 12:
         del B
         torch.cuda.empty_cache()
         m360 = synth.workload_spd_large()
         e360 = float(m360.nbf) ** 4
-        prec360 = "split_f16_8" if args.precision == "split_f16" else args.precision
+        prec360 = args.precision
         p360 = lrtei.Plan(m360, prec360)
         B360 = torch.empty((m360.nbf ** 2, m360.nbf ** 2), dtype=torch.float64, device="cuda")
         p360.assemble_B(args.form, out=B360)
@@ -669,8 +669,8 @@ def run_ours(args, world, rank, local):
             cpu["jbuild_sample"] = jsample
 
     if rank == 0:
-        dtype = {"split_f16": "f16x3 (8+11+11-bit integer slices, fp32 acc)",
-                 "split_f16_8": "f16x3 (8+11+11-bit integer slices, 8 products, 3 fp32 accumulators)",
+        dtype = {"split_f16": "f16x3 (8+12+12-bit integer slices, fp32 acc)",
+                 "split_f16_8": "f16x3 (8+12+12-bit integer slices, 8 products, 3 fp32 accumulators)",
                  "bf16": "bf16", "fp64": "f64", "fp32": "f32"}[
             args.precision]
         line = {
@@ -752,7 +752,8 @@ def run_kr(args, mol, B, world, have_fp64_B=False):
     nb2 = mol.nbf * mol.nbf
     Bref = B.clone() if have_fp64_B and B.numel() * 8 < 12e9 else None
     # The compressed factors' rows are graded (their weight sits in the columns of the largest
-    # singular values); six-product slices measured 1.5e-7 on them, so this leg runs eight products.
+    # singular values); six-product slices measured 9e-8 on them, at the edge of the 1e-7 bound, so
+    # this leg runs eight products (9e-10).
     prec = "split_f16_8" if args.precision == "split_f16" else args.precision
     pk = lrtei.Plan(mol, prec)
     t0 = time.perf_counter()

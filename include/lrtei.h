@@ -58,15 +58,16 @@ typedef enum {
   LRTEI_FP64 = 0,        /* FP64 CUDA-core contractions */
   LRTEI_FP32 = 1,        /* FP32 CUDA-core contractions */
   LRTEI_SPLIT_F16 = 2,  /* tcgen05 tensor cores, split operands: per row a power-of-two scale and
-                            three integer slices (8 + 11 + 11 bits) held exactly in 16-bit floats;
-                            the leading products accumulate exactly in FP32 within each 256-deep K
-                            chunk, chunks are summed in int32 / FP32 registers (about 30 bits) */
+                            three integer slices (8 + 12 + 12 bits) held exactly in 16-bit floats;
+                            the leading products accumulate exactly in FP32 within each 128-deep K
+                            chunk, chunks are summed in int32 / FP32 registers (about 32 bits);
+                            1e-8 to 5e-8 measured */
   LRTEI_BF16 = 3,        /* tcgen05 tensor cores, plain BF16 operands (one rounding per element),
                             FP32 accumulation */
   LRTEI_SPLIT_F16_8 = 4  /* as LRTEI_SPLIT_F16, plus the two next-order slice products (t1 t2 and
                             t2 t1), with the small terms in a third accumulator: 8 tensor-core
-                            products per K step instead of 6 and 128 x 64 tiles, an error about
-                            seven times smaller (1e-9 to 2e-8 measured) */
+                            products per K step instead of 6 and 128 x 64 tiles, an error several
+                            times smaller (1e-9 to 1.5e-8 measured) */
 } lrtei_precision;
 
 /* Which of the two equivalent forms of Theorem 1 assembles B.  On the FP64 and FP32 paths both

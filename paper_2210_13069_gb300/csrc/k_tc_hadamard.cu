@@ -6,7 +6,7 @@
 // Each G_{d,p} tile is a product of depth K = n (padded to 32 or 64) in the split-precision
 // format of the GEMM (k_tcgen05.cu): three FP16 integer slices of T_{d,p}, four of S_d, six MMAs per
 // 16-deep step into two FP32 TMEM accumulators, L0 (exact) and L12 (the lower-order products).
-// The epilogue warps form g_d = L0 + L12 / 2^11 per dimension as a pair of FP32 numbers, the
+// The epilogue warps form g_d = L0 + L12 / 2^12 per dimension as a pair of FP32 numbers, the
 // product over d and the weighted sum over the nodes in FP32 pairs (Dekker-style products with
 // fmaf, Knuth's two-sum), and store each tile of B_u once in FP64, with its mirror.
 //
@@ -312,9 +312,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const float gh = __uint_as_float(l0[j]);                      // exact integer sum
-              const float gl = __uint_as_float(l12[j]) * (1.0f / 2048.0f);  // exact scaling
+              const float gl = __uint_as_float(l12[j]) * (1.0f / 4096.0f);  // exact scaling
               if (d == 0) {
-                // f g: f is a normalised pair, so its trailing part times gl (2^-33) is dropped
+                // f g: f is a normalised pair, so its trailing part times gl (below 2^-33) is dropped
                 const float t = f.x * gh;
                 float e = fmaf(f.x, gh, -t);
                 e = fmaf(f.x, gl, e);
@@ -379,7 +379,7 @@ __global__ void k_scale_rows(const double* __restrict__ S, const double* __restr
 }
 
 // One warp per row of n <= 64 FP64 values: the row exponent (max|x| 256/255 < 2^e, as the GEMM's
-// slicing) and the three slices, zero padded to kpad; t1 / 2^11 too when s1h is given.  An all-zero
+// slicing) and the three slices, zero padded to kpad; t1 / 2^12 too when s1h is given.  An all-zero
 // row gets kZeroRowExpo.
 __global__ void k_slice_short_rows(const double* __restrict__ src, int64_t rows, int n, int kpad,
                                    uint16_t* __restrict__ s0, uint16_t* __restrict__ s1, uint16_t* __restrict__ s2,

@@ -3,20 +3,22 @@
 // C = scale * A B^T for FP64 matrices A (M x K) and B (N x K), both K-contiguous, through
 // integer slices held in FP16 (every slice is an integer or an integer times a power of two,
 // so the FP16 values are exact):
-//   x = 2^e (s0 2^-8 + t1 2^-19 + t2 2^-30),  e per row,  |s0| <= 255, |t1|, |t2| <= 1024.
-// Per 256-deep K chunk the tensor cores accumulate in TMEM (FP32):
-//   L0  = sum s0a s0b                      (products < 2^16, 256 of them: exact in FP32)
-//   L12 = sum s0a t1b + s0a t2'b + t1a s0b + t1a t1'b + t2'a s0b,   t' = t / 2^11
+//   x = 2^e (s0 2^-8 + t1 2^-20 + t2 2^-32),  e per row,  |s0| <= 255, |t1|, |t2| <= 2048.
+// Per 128-deep K chunk the tensor cores accumulate in TMEM (FP32):
+//   L0  = sum s0a s0b                      (products < 2^16, 128 of them: exact in FP32)
+//   L12 = sum s0a t1b + s0a t2'b + t1a s0b + t1a t1'b + t2'a s0b,   t' = t / 2^12
 // and the epilogue warps drain each chunk into registers: L0 into an int32 running sum
 // (exact for K <= 32768), L12 into an FP32 running sum.  The tile is written as
-//   C = scale 2^(ea+eb-16) (T0 + T12 / 2^11)  in FP64.
+//   C = scale 2^(ea+eb-16) (T0 + T12 / 2^12)  in FP64.
 // The leading term is exact whatever rounding the tensor core applies to its FP32 sums; the
-// rest carries 2^-11 of the weight.  The representation error is about 2^-31 of the row
-// maxima; the dropped products (t1 t2, t2 t1, t2 t2) are below 2^-29 of them.
+// rest carries 2^-12 of the weight.  The representation error is about 2^-33 of the row
+// maxima; the dropped products (t1 t2, t2 t1, t2 t2) are about 2^-29 of them.
 // The tensor core's FP32 accumulation truncates (measured against an emulation), so L12's
-// smaller terms are cut at the scale of its s0 t1 terms.  The eight-product variant (P8) keeps
-// t1 t2 and t2 t1 as well and splits L12 into L1 = s0 t1 + t1 s0 and L2 (the rest, in its own
-// accumulator): three accumulators per buffer, 128 x 64 tiles, C from T0 + (T1 + T2) / 2^11.
+// smaller terms are cut at the scale of its s0 t1 terms, and the truncation error of a chunk
+// grows with the chunk's depth: hence chunks of 128 rather than the 512 that L0's exactness
+// would allow.  The eight-product variant (P8) keeps t1 t2 and t2 t1 as well and splits L12 into
+// L1 = s0 t1 + t1 s0 and L2 (the rest, in its own accumulator): three accumulators per buffer,
+// 128 x 64 tiles, C from T0 + (T1 + T2) / 2^12.
 //
 // Kernel organisation (persistent: one CTA per SM walks 128 x BN output tiles, BN = 128 for
 // wide outputs, 18 warps):
@@ -50,7 +52,7 @@ namespace lrtei {
 namespace tc {
 
 constexpr int BM = 128;      // rows of A per tile (MMA M)
-constexpr int KCHUNK = 256;  // K per exact FP32 accumulation chunk
+constexpr int KCHUNK = 128;  // K per accumulation chunk drained by the epilogue
 // K per pipeline stage, BK: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte rows, 64-byte
 // swizzle, smaller stages so more of them fit in shared memory).
 constexpr int NA = 3;        // A slices: s0, t1, t2'
@@ -100,11 +102,11 @@ __device__ __forceinline__ double pow2(int k) {  // 2^k, exponent clamped to the
   return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
-// (T0 + T12 / 2^11) 2^k in integer arithmetic (this device's FP64 rate would make an FP64
-// epilogue a visible part of the GEMM): X = T0 2^20 + round(T12 2^9) is an integer below 2^53
-// (|T0| < 2^31; |T12| < 2^34 for K <= 32768), so X 2^(k-20) is exact in FP64 and is built from
-// its bits.  Rounding T12 to 2^-9 moves the result by at most 2^-21 of a unit of T0, far below
-// the 2^-31 representation error of the operands.  Results below the normal range flush to 0.
+// (T0 + T12 / 2^12) 2^k in integer arithmetic (this device's FP64 rate would make an FP64
+// epilogue a visible part of the GEMM): X = T0 2^21 + round(T12 2^9) is an integer below 2^53
+// (|T0| < 2^31; |T12| < 2^36 for K <= 32768), so X 2^(k-21) is exact in FP64 and is built from
+// its bits.  Rounding T12 to 2^-9 moves the result by at most 2^-22 of a unit of T0, far below
+// the 2^-33 representation error of the operands.  Results below the normal range flush to 0.
 // round(f 2^9) as an integer, from the bits of the FP32 value f.
 __device__ __forceinline__ int64_t round_2p9(float f) {
   const uint32_t fb = __float_as_uint(f);
@@ -124,18 +126,18 @@ __device__ __forceinline__ int64_t round_2p9(float f) {
 
 // t2: a second FP32 sum of the same weight as t12 (the three-accumulator scheme), else 0.
 __device__ __forceinline__ double combine_pow2(int t0, float t12, int k, float t2 = 0.f) {
-  const int64_t X = ((int64_t)t0 << 20) + round_2p9(t12) + round_2p9(t2);
+  const int64_t X = ((int64_t)t0 << 21) + round_2p9(t12) + round_2p9(t2);
   if (X == 0) return 0.0;
   const uint64_t a = (uint64_t)(X < 0 ? -X : X);
   const int lz = __clzll((long long)a);    // a < 2^53: lz >= 11
   const uint64_t mant = a << (lz - 11);    // leading one at bit 52
-  const int E = 1023 + (63 - lz) + k - 20;  // X 2^(k-20) = 1.f 2^(E-1023)
+  const int E = 1023 + (63 - lz) + k - 21;  // X 2^(k-21) = 1.f 2^(E-1023)
   if (E <= 0) return 0.0;
   const uint64_t bits = ((uint64_t)(X < 0) << 63) | ((uint64_t)min(E, 2046) << 52) | (mant & ((1ULL << 52) - 1));
   return __longlong_as_double((long long)bits);
 }
 
-// Output element of a staged tile: scale 2^k (T0 + T12 / 2^11), or scale 2^k T12 for plain BF16.
+// Output element of a staged tile: scale 2^k (T0 + T12 / 2^12), or scale 2^k T12 for plain BF16.
 template <bool PLAIN, bool P8>
 __device__ __forceinline__ double tile_value(const int* st0, const float* st12, const float* st2, int i, int k,
                                             double scale) {
@@ -205,8 +207,8 @@ __device__ __forceinline__ Work work_item(const Params& p, int64_t item) {
 // through the ring's shared memory (idle then: the producer waits for the epilogue's "staged
 // tile stored" barrier before it loads the next tile), then stored coalesced.
 // PLAIN: one BF16 operand plane each, one product per k step, FP32 sums (no exactness).
-// P8: eight products per k step (the next-order terms t1 t2' / 2^11 and t2' t1 / 2^11 kept, with
-// a fourth A slice t1 / 2^11) into three accumulators.
+// P8: eight products per k step (the next-order terms t1' t2' and t2' t1' kept, with a fourth A
+// slice t1' = t1 / 2^12) into three accumulators.
 template <int BN, int BK, int STAGES, bool PLAIN, bool P8>
 __global__ void __launch_bounds__(block_threads<BN>(), 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
@@ -353,8 +355,8 @@ __global__ void __launch_bounds__(block_threads<BN>(), 1)
                 mma_bf16_a<ACol::lastuse>(d2, a1 + o, b1h + o, idesc, 1u);
                 if constexpr (P8) {
                   mma_bf16_a<ACol::fill>(d2, a2 + o, b0 + o, idesc, 1u);
-                  mma_bf16_a<ACol::lastuse>(d2, a2 + o, b1h + o, idesc, 1u);  // t2' t1 / 2^11
-                  mma_bf16(d2, a1h + o, b2 + o, idesc, 1u);                  // t1 / 2^11 t2'
+                  mma_bf16_a<ACol::lastuse>(d2, a2 + o, b1h + o, idesc, 1u);  // t2' t1'
+                  mma_bf16(d2, a1h + o, b2 + o, idesc, 1u);                  // t1' t2'
                 } else {
                   mma_bf16(d1, a2 + o, b0 + o, idesc, 1u);
                 }
@@ -1181,7 +1183,7 @@ static lrtei_status tc_gemm_impl(const SplitMatrix& A, const SplitMatrix& B, int
     return LRTEI_ERR_ARG;
   }
   if (A.eight && !A.s1h) {
-    set_error("tc_gemm: the eight-product scheme needs the A operand's t1 / 2^11 plane");
+    set_error("tc_gemm: the eight-product scheme needs the A operand's t1 / 2^12 plane");
     return LRTEI_ERR_ARG;
   }
   lrtei_status s;

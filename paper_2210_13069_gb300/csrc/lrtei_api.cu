@@ -685,7 +685,7 @@ void release_split(lrtei_plan* pl, SplitMatrix& m) {
   m = SplitMatrix();
 }
 
-// F_u slices.  The fourth plane (t1 / 2^11) is only needed when F_u is the B operand (the
+// F_u slices.  The fourth plane (t1 / 2^12) is only needed when F_u is the B operand (the
 // assembly B_u = G F_u^T); J-builds use F_u as the A operand only.
 lrtei_status ensure_Fsp(lrtei_plan* pl, cudaStream_t st, bool need_s1h) {
   if (pl->have_Fsp && (!need_s1h || pl->Fsp.plain || pl->Fsp.s1h)) return LRTEI_OK;

@@ -152,18 +152,18 @@ __device__ __forceinline__ uint16_t f16_bits(float f) {
   return *reinterpret_cast<uint16_t*>(&h);
 }
 
-// round(x 2^(30 - e)) as an integer, from the bit pattern of x (no FP64 arithmetic: this
+// round(x 2^(32 - e)) as an integer, from the bit pattern of x (no FP64 arithmetic: this
 // device's FP64 rate would make the slicing ALU-bound).  For |x| < 2^e 255/256 the result is
-// below 255 * 2^22 in magnitude; zeros and subnormals give 0.
-__device__ __forceinline__ int64_t fixed30(double x, int e) {
+// below 255 * 2^24 in magnitude; zeros and subnormals give 0.
+__device__ __forceinline__ int64_t fixed32(double x, int e) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
   if (E == 0) return 0;
   const uint64_t m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);  // x = +-m 2^(E-1075)
-  const int sh = E - 1075 + 30 - e;
+  const int sh = E - 1075 + 32 - e;
   int64_t q;
   if (sh >= 0)
-    q = (int64_t)(m << (sh > 11 ? 11 : sh));  // not reached for |x| < 2^e (then sh <= -22)
+    q = (int64_t)(m << (sh > 9 ? 9 : sh));  // not reached for |x| < 2^e (then sh < -20)
   else if (sh < -62)
     q = 0;
   else
@@ -171,26 +171,27 @@ __device__ __forceinline__ int64_t fixed30(double x, int e) {
   return (b >> 63) ? -q : q;
 }
 
-// Slices of one element: q = round(x 2^(30-e)), s0 = round(q / 2^22), r = q - s0 2^22,
-// t1 = round(r / 2^11), t2 = r - t1 2^11; x ~ 2^e (s0 2^-8 + t1 2^-19 + t2 2^-30).
-// Stored as FP16: s0, t1, t2 / 2^11 and (optionally) t1 / 2^11 -- all exact.
+// Slices of one element: q = round(x 2^(32-e)), s0 = round(q / 2^24), r = q - s0 2^24,
+// t1 = round(r / 2^12), t2 = r - t1 2^12; x ~ 2^e (s0 2^-8 + t1 2^-20 + t2 2^-32), |s0| <= 255,
+// |t1|, |t2| <= 2048.  Stored as FP16: s0, t1, t2 / 2^12 and (optionally) t1 / 2^12 -- all exact
+// (integers up to 2^11 in magnitude, and those times 2^-12).
 __device__ __forceinline__ void slice_store(double x, int e, bool live, int nslices, int64_t o, uint16_t* s0,
                                             uint16_t* s1, uint16_t* s2, uint16_t* s1h) {
   float a = 0.f, b = 0.f, c = 0.f;
   if (live) {
-    const int64_t q = fixed30(x, e);
-    const int64_t q0 = (q + (1LL << 21)) >> 22;
-    const int64_t r = q - (q0 << 22);
-    const int64_t q1 = (r + (1LL << 10)) >> 11;
-    const int64_t q2 = r - (q1 << 11);
+    const int64_t q = fixed32(x, e);
+    const int64_t q0 = (q + (1LL << 23)) >> 24;
+    const int64_t r = q - (q0 << 24);
+    const int64_t q1 = (r + (1LL << 11)) >> 12;
+    const int64_t q2 = r - (q1 << 12);
     a = (float)q0;
     b = nslices > 1 ? (float)q1 : 0.f;
     c = nslices > 2 ? (float)q2 : 0.f;
   }
   s0[o] = f16_bits(a);
   s1[o] = f16_bits(b);
-  s2[o] = f16_bits(c * (1.0f / 2048.0f));
-  if (s1h) s1h[o] = f16_bits(b * (1.0f / 2048.0f));
+  s2[o] = f16_bits(c * (1.0f / 4096.0f));
+  if (s1h) s1h[o] = f16_bits(b * (1.0f / 4096.0f));
 }
 
 // ------------------------------------------------------------------ FP32 pairs to FP64

@@ -77,7 +77,7 @@ def test_batched_graph_after_operands_rebuilt(lib):
         lib.lrtei_jbuild_batched([p.plan for p in plans], Ds, Rs, Js)
     torch.cuda.synchronize()
     first = [J.clone() for J in Js]
-    B = plans[0].assemble_B()  # rebuilds the slices of F_u and K with the t1 / 2^11 plane
+    B = plans[0].assemble_B()  # rebuilds the slices of F_u and K with the t1 / 2^12 plane
     for _ in range(2):
         for J in Js:
             J.fill_(float("nan"))

@@ -12,7 +12,7 @@ the oracle's numpy form of the same equations (oracle/kr.py).
   uncompressed FP64 GPU path, and the compression error alone (FP64), stated.  The six-product
   split on compressed factors is stated too: its rows are graded (their weight sits in the few
   columns of the largest singular values), which per-row fixed-point slices represent less well
-  than the flat rows of the uncompressed factors (1.5e-7 measured, over the bound).
+  than the flat rows of the uncompressed factors (9e-8 measured, at the edge of the bound).
 """
 import numpy as np
 import pytest

@@ -1,8 +1,8 @@
-"""The 360-function instance (24 atoms, omega = 0.33, n = 24, P = 32) through the eight-product
-split-F16 tensor-core path: the full 129 600 x 129 600 FP64 B (134 GB) is assembled, its sampled
-rows are checked against the oracle (two rows) and against the FP64 GPU path (four rows), and
-its exact symmetry on sampled entries.  Tolerance: relative Frobenius 1e-7 per set of rows (the
-six-product scheme measured 1.06e-7 on the two oracle rows of this instance)."""
+"""The 360-function instance (24 atoms, omega = 0.33, n = 24, P = 32) through the split-F16
+tensor-core path, with eight and with six products: the full 129 600 x 129 600 FP64 B (134 GB)
+is assembled, its sampled rows are checked against the oracle (two rows) and against the FP64
+GPU path (four rows), and its exact symmetry on sampled entries.  Tolerance: relative Frobenius
+1e-7 per set of rows."""
 import numpy as np
 import pytest
 
@@ -16,7 +16,8 @@ def rel_fro(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def test_split_f16_8_full_size_360():
+@pytest.mark.parametrize("precision", ["split_f16_8", "split_f16"])
+def test_split_full_size_360(precision):
     import torch
     from paper_2210_13069_gb300 import build_lib, lrtei
     assert torch.cuda.is_available(), "GPU test"
@@ -25,7 +26,7 @@ def test_split_f16_8_full_size_360():
     m = synth.workload_spd_large()
     nbf = m.nbf
     assert nbf == 360
-    pl = lrtei.Plan(m, "split_f16_8")
+    pl = lrtei.Plan(m, precision)
     B = pl.assemble_B()
     torch.cuda.synchronize()
     pl.status()
@@ -50,5 +51,5 @@ def test_split_f16_8_full_size_360():
     o = oracle.Oracle.from_molecule(m)
     oref = o.B_rows([picks[1][0] * nbf + picks[1][1], picks[3][0] * nbf + picks[3][1]])
     eor = rel_fro([rows[picks[1]], rows[picks[3]]], oref)
-    print(f"split_f16_8 360 functions: sampled rows vs FP64 GPU {e64:.3e}, vs oracle {eor:.3e}")
+    print(f"{precision} 360 functions: sampled rows vs FP64 GPU {e64:.3e}, vs oracle {eor:.3e}")
     assert e64 <= 1e-7 and eor <= 1e-7

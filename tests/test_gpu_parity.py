@@ -251,7 +251,7 @@ def test_full_size_180_sampled_rows(lib):
 
 @pytest.mark.parametrize("maker", ["small_s", "spd_small", "ragged"])
 def test_split_f16_full_B(lib, maker):
-    """tcgen05 path (8+11+11-bit integer slices, exact leading products): rel. Frobenius <= 1e-7."""
+    """tcgen05 path (8+12+12-bit integer slices, exact leading products): rel. Frobenius <= 1e-7."""
     m = {"small_s": synth.workload_small_s, "spd_small": mol_spd_small, "ragged": mol_ragged}[maker]()
     ref = oracle.Oracle.from_molecule(m).assemble_B()
     pl = lib.Plan(m, "split_f16")
