@@ -68,23 +68,60 @@ __global__ void __launch_bounds__(1024) k_split_rows_reg(const double* __restric
     slice_store(0.0, e, false, nslices, r * kpad + i, s0, s1, s2, s1h);
 }
 
-// Long rows: two passes over the row (maximum, then slices).
-__global__ void k_split_rows(const double* __restrict__ src, int64_t rows, int64_t k, int64_t ld, int64_t kpad,
-                             uint16_t* __restrict__ s0, uint16_t* __restrict__ s1, uint16_t* __restrict__ s2,
-                             uint16_t* __restrict__ s1h, int* __restrict__ expo, int nslices) {
+// Long rows: two passes over the row (maximum, then slices), four consecutive elements per thread
+// and step: 16-byte loads where the rows allow them (even ld, 16-byte aligned source) and one
+// 8-byte store per plane (kpad is a multiple of 4).
+__global__ void __launch_bounds__(256) k_split_rows4(const double* __restrict__ src, int64_t rows, int64_t k,
+                                                     int64_t ld, int64_t kpad, uint16_t* __restrict__ s0,
+                                                     uint16_t* __restrict__ s1, uint16_t* __restrict__ s2,
+                                                     uint16_t* __restrict__ s1h, int* __restrict__ expo, int nslices) {
   __shared__ uint64_t red[32];
   const int64_t r = blockIdx.x;
   const double* x = src + r * ld;
+  const bool vec = (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+  constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFULL;
   uint64_t mx = 0;
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
-    const uint64_t a = (uint64_t)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFULL;
-    mx = a > mx ? a : mx;
+  for (int64_t i = 4 * (int64_t)threadIdx.x; i < k; i += 4 * (int64_t)blockDim.x) {
+    if (vec && i + 3 < k) {
+      const double2 a = *reinterpret_cast<const double2*>(x + i);
+      const double2 b = *reinterpret_cast<const double2*>(x + i + 2);
+      const uint64_t m0 = (uint64_t)__double_as_longlong(a.x) & kMag, m1 = (uint64_t)__double_as_longlong(a.y) & kMag;
+      const uint64_t m2 = (uint64_t)__double_as_longlong(b.x) & kMag, m3 = (uint64_t)__double_as_longlong(b.y) & kMag;
+      const uint64_t u = m0 > m1 ? m0 : m1, w = m2 > m3 ? m2 : m3;
+      const uint64_t t = u > w ? u : w;
+      mx = t > mx ? t : mx;
+    } else {
+      for (int j = 0; j < 4 && i + j < k; ++j) {
+        const uint64_t a = (uint64_t)__double_as_longlong(x[i + j]) & kMag;
+        mx = a > mx ? a : mx;
+      }
+    }
   }
   bool nz;
   const int e = row_exponent(mx, red, nz);
   if (threadIdx.x == 0) expo[r] = e;
-  for (int64_t i = threadIdx.x; i < kpad; i += blockDim.x)
-    slice_store(i < k ? x[i] : 0.0, e, i < k && nz, nslices, r * kpad + i, s0, s1, s2, s1h);
+  for (int64_t i = 4 * (int64_t)threadIdx.x; i < kpad; i += 4 * (int64_t)blockDim.x) {
+    double v[4];
+    if (vec && i + 3 < k) {
+      const double2 a = *reinterpret_cast<const double2*>(x + i);
+      const double2 b = *reinterpret_cast<const double2*>(x + i + 2);
+      v[0] = a.x;
+      v[1] = a.y;
+      v[2] = b.x;
+      v[3] = b.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = i + j < k ? x[i + j] : 0.0;
+    }
+    SliceBits q[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) q[j] = slice_bits(v[j], e, i + j < k && nz, nslices);
+    const int64_t o = r * kpad + i;
+    *reinterpret_cast<ushort4*>(s0 + o) = make_ushort4(q[0].s0, q[1].s0, q[2].s0, q[3].s0);
+    *reinterpret_cast<ushort4*>(s1 + o) = make_ushort4(q[0].s1, q[1].s1, q[2].s1, q[3].s1);
+    *reinterpret_cast<ushort4*>(s2 + o) = make_ushort4(q[0].s2, q[1].s2, q[2].s2, q[3].s2);
+    if (s1h) *reinterpret_cast<ushort4*>(s1h + o) = make_ushort4(q[0].s1h, q[1].s1h, q[2].s1h, q[3].s1h);
+  }
 }
 
 // Few long rows (fewer rows than SMs, e.g. the R density rows of a J-build): a cluster of
@@ -195,14 +232,14 @@ void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld,
     return;
   }
   // Rows of up to 4096 elements stay in registers (one read); longer rows take two passes with
-  // 256 threads, more rows in flight per SM: 1.55 against 1.85 ms for the 16 290 rows of 13 824
-  // of G at N_b = 180 (the second pass reads the row from L2).
+  // 256 threads, more rows in flight per SM (the second pass reads the row from L2).  The padded
+  // length is a multiple of 256 here (kpad256).
   if (k <= 4096)
     tc::k_split_rows_reg<4><<<(unsigned)rows, 1024, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h,
                                                             m.expo, nslices);
   else
-    tc::k_split_rows<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h, m.expo,
-                                                     nslices);
+    tc::k_split_rows4<<<(unsigned)rows, 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2, s1h, m.expo,
+                                                      nslices);
 }
 
 void launch_transpose(const double* in, int64_t rows, int64_t cols, int64_t ldi, double* out, int64_t ldo,

@@ -173,10 +173,12 @@ __device__ __forceinline__ int64_t fixed32(double x, int e) {
 
 // Slices of one element: q = round(x 2^(32-e)), s0 = round(q / 2^24), r = q - s0 2^24,
 // t1 = round(r / 2^12), t2 = r - t1 2^12; x ~ 2^e (s0 2^-8 + t1 2^-20 + t2 2^-32), |s0| <= 255,
-// |t1|, |t2| <= 2048.  Stored as FP16: s0, t1, t2 / 2^12 and (optionally) t1 / 2^12 -- all exact
+// |t1|, |t2| <= 2048.  As FP16 bit patterns: s0, t1, t2 / 2^12 and t1 / 2^12 -- all exact
 // (integers up to 2^11 in magnitude, and those times 2^-12).
-__device__ __forceinline__ void slice_store(double x, int e, bool live, int nslices, int64_t o, uint16_t* s0,
-                                            uint16_t* s1, uint16_t* s2, uint16_t* s1h) {
+struct SliceBits {
+  uint16_t s0, s1, s2, s1h;
+};
+__device__ __forceinline__ SliceBits slice_bits(double x, int e, bool live, int nslices) {
   float a = 0.f, b = 0.f, c = 0.f;
   if (live) {
     const int64_t q = fixed32(x, e);
@@ -188,10 +190,16 @@ __device__ __forceinline__ void slice_store(double x, int e, bool live, int nsli
     b = nslices > 1 ? (float)q1 : 0.f;
     c = nslices > 2 ? (float)q2 : 0.f;
   }
-  s0[o] = f16_bits(a);
-  s1[o] = f16_bits(b);
-  s2[o] = f16_bits(c * (1.0f / 4096.0f));
-  if (s1h) s1h[o] = f16_bits(b * (1.0f / 4096.0f));
+  return {f16_bits(a), f16_bits(b), f16_bits(c * (1.0f / 4096.0f)), f16_bits(b * (1.0f / 4096.0f))};
+}
+
+__device__ __forceinline__ void slice_store(double x, int e, bool live, int nslices, int64_t o, uint16_t* s0,
+                                            uint16_t* s1, uint16_t* s2, uint16_t* s1h) {
+  const SliceBits q = slice_bits(x, e, live, nslices);
+  s0[o] = q.s0;
+  s1[o] = q.s1;
+  s2[o] = q.s2;
+  if (s1h) s1h[o] = q.s1h;
 }
 
 // ------------------------------------------------------------------ FP32 pairs to FP64
