@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-nb360", action="store_true")
     ap.add_argument("--no-uncontracted", action="store_true")
+    ap.add_argument("--no-exchange", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true")
     ap.add_argument("--natoms", type=int, default=12, help="scaled-down runs (profiling only)")
     ap.add_argument("--kr-eps", type=float, default=1e-8,
                     help="Khatri-Rao compression threshold of the compressed-form leg (0: leg off)")
@@ -575,6 +577,16 @@ def run_ours(args, world, rank, local):
     if not args.no_uncontracted and args.precision == "split_f16":
         unc = run_uncontracted(args, B, world)
 
+    # ---- the long-range exchange of the same workload (appendix, eq. exchange)
+    exch = None
+    if not args.no_exchange and args.natoms == 12 and not args.no_fp64:
+        exch = run_exchange(args, mol, world)
+
+    # ---- adaptive integration boxes (Section 6) for the same workload
+    adapt = None
+    if not args.no_adaptive and args.natoms == 12:
+        adapt = run_adaptive(args, mol, plan, B, ms, world)
+
     # ---- the same step with the eight-product scheme (error several times smaller)
     split8 = None
     if args.precision == "split_f16" and not args.no_fp64:
@@ -683,7 +695,7 @@ def run_ours(args, world, rank, local):
                        "entries_per_step": entries_per_step, "unique_entries": (npair * (npair + 1)) // 2,
                        "l2": "no flush needed: the 8.4 GB output per step is far larger than the 129 MB L2",
                        "parallelism": f"replicas x{world} (independent problems)"},
-            "jbuilds": jb, "kr_compressed": kr, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "uncontracted_hadamard_tc": unc, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "jbuilds": jb, "kr_compressed": kr, "fp64_same_gpu": fp64, "split_f16_8": split8, "screening": screening, "uncontracted_hadamard_tc": unc, "exchange": exch, "adaptive": adapt, "batched": batched, "nb20": nb20, "nb360": nb360, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches), "cuda_core_peaks": fma_peaks,
         }
         print(json.dumps(line), flush=True)
@@ -691,6 +703,120 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_exchange(args, mol, world, seed: int = 7):
+    """Long-range exchange K^lr = 2 sum_j X_j K X_j^T (eq. exchange) of the workload for N_b / 2
+    orbitals: time per K^lr in the bench's precision and in FP64 on the same GPU, the error against
+    the FP64 result, and the rate in the method's flops (X = Q M^T and K^lr = 2 Y_p X_p^T at
+    2 N_orb N_b^2 n^3 each, Y = X K by mode products at 6 P n^4 per row of X) and in the dense-K
+    products the tensor cores issue (the split scheme's products counted once)."""
+    import numpy as np
+    import torch
+    from paper_2210_13069_gb300 import lrtei
+    stream = torch.cuda.current_stream()
+    nbf, n, P = mol.nbf, mol.n, mol.P
+    norb = nbf // 2
+    rng = np.random.default_rng(seed)
+    Q = torch.as_tensor(rng.normal(0.0, 1.0 / math.sqrt(nbf), size=(norb, nbf)), device="cuda")
+    n3 = float(n) ** 3
+    alg = 4.0 * norb * nbf * nbf * n3 + 6.0 * P * float(n) ** 4 * norb * nbf
+    dense = 4.0 * norb * nbf * nbf * n3 + 2.0 * norb * nbf * n3 * n3
+    res = {}
+    for prec in (args.precision, "fp64"):
+        pl = lrtei.Plan(mol, prec)
+        K = pl.exchange(Q)  # builds the plan's operands
+        torch.cuda.synchronize()
+        reps = 1 if prec == "fp64" else 3
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        e0.record(stream)
+        for _ in range(reps):
+            pl.exchange(Q, out=K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pl.status()
+        res[prec] = (K, max_over_ranks(e0.elapsed_time(e1) / reps, world, device="cuda"))
+        pl.close()
+    K, ms = res[args.precision]
+    K64, ms64 = res["fp64"]
+    peak = measured_peaks()[0]["bf16_tflops_sustained"]
+    out = {"workload": f"{WORKLOAD.split(':')[0]}, {norb} orbitals (N(0, 1/N_b) coefficients)",
+           "precision": args.precision, "orbitals": norb, "ms": ms, "exchanges_per_s": world * 1e3 / ms,
+           "fp64_ms": ms64, "speedup_vs_fp64": ms64 / ms,
+           "rel_err_vs_fp64": float(torch.linalg.norm(K - K64) / torch.linalg.norm(K64)),
+           "alg_flops": alg, "alg_tflops": alg / (ms * 1e-3) / 1e12, "frac_alg": alg / (ms * 1e-3) / 1e12 / peak,
+           "dense_K_flops": dense, "dense_tflops": dense / (ms * 1e-3) / 1e12,
+           "peak_tflops": peak, "peak_kind": "measured (bf16_tflops_sustained)"}
+    del res, K, K64
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_adaptive(args, mol, plan, B, ms_fixed, world, tau=1e-20, npart=4):
+    """Adaptive integration boxes (Section 6): the workload's unique pairs in npart partitions by
+    their numerical supports at tau_adaptive = 1e-20, one coefficient block per partition pair;
+    time per B in the bench's precision against the fixed-box step, the tensor-core GEMM time and
+    launches within it, how far B moves from the fixed-box B, and both against a high-order
+    fixed-box FP64 plan (n = P = 64; n = 48 beside it shows how far that reference has converged)
+    on 4096 sampled entries (Algorithm 1 on the GPU)."""
+    import numpy as np
+    import torch
+    from paper_2210_13069_gb300 import lrtei
+    stream = torch.cuda.current_stream()
+    plan.assemble_B(args.form, out=B)
+    Bfix = B.clone()
+    pa = lrtei.Plan(mol, args.precision, adaptive=(tau, npart))
+    info = pa.info
+    pa.assemble_B("auto", out=B)
+    torch.cuda.synchronize()
+    lrtei.lrtei_profile_reset()
+    lrtei.lrtei_profile_enable(True)
+    reps = 2
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(reps):
+        pa.assemble_B("auto", out=B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms, g_cnt = lrtei.lrtei_profile_get("tc_gemm")
+    lrtei.lrtei_profile_enable(False)
+    lrtei.lrtei_profile_reset()
+    pa.status()
+    ms = max_over_ranks(e0.elapsed_time(e1) / reps, world, device="cuda")
+    num = den = 0.0
+    for i in range(0, B.shape[0], 4096):
+        num += float(torch.linalg.norm(B[i:i + 4096] - Bfix[i:i + 4096])) ** 2
+        den += float(torch.linalg.norm(Bfix[i:i + 4096])) ** 2
+    nbf = mol.nbf
+    idx = np.random.default_rng(11).integers(0, nbf, size=(4096, 4)).astype(np.int32)
+    refs = {}
+    for nh in (48, 64):
+        ph = lrtei.Plan(mol, "fp64", n=nh, P=64)
+        refs[nh] = ph.entries(idx)
+        ph.status()
+        ph.close()
+    it = torch.as_tensor(idx.astype(np.int64), device="cuda")
+    rr, cc = it[:, 0] * nbf + it[:, 1], it[:, 2] * nbf + it[:, 3]
+    ref = refs[64]
+
+    def rel(x):
+        return float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref))
+    nb2 = float(mol.nbf) ** 2
+    out = {"tau_adaptive": tau, "partitions": int(info["npartitions"]),
+           "partition_half_widths": [float(b) for b in info["partition_b"]][:int(info["npartitions"])],
+           "precision": args.precision, "ms_per_B": ms, "entries_per_s": whole_job_rate(nb2 * nb2, world, ms, device="cuda"),
+           "fixed_box_ms_per_B": ms_fixed, "tc_gemm_ms_per_B": g_ms / reps, "tc_gemm_launches_per_B": g_cnt / reps,
+           "rel_change_vs_fixed_box_B": math.sqrt(num / den),
+           "sampled_entries_vs_n64_fixed_box_fp64": {"adaptive": rel(B[rr, cc]), "fixed_box": rel(Bfix[rr, cc]),
+                                                    "n48_reference": rel(refs[48])}}
+    pa.close()
+    del Bfix
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_uncontracted(args, B, world):

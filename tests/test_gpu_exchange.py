@@ -5,7 +5,7 @@ orbital coefficients), which the CPU pins tie to the erf-Boys closed forms.
 Tolerances (relative Frobenius): FP64 path 1e-12; split-F16 1e-7.  Orbitals in one block and in
 several (LRTEI_EXCHANGE_BLOCK); a Khatri-Rao compressed plan against the same contraction of the
 oracle's compressed B; the 180-function workload with 90 orbitals against the FP64 GPU path
-(eight products within 1e-7).
+(six and eight products within 1e-7).
 """
 import numpy as np
 import pytest
@@ -86,8 +86,9 @@ def test_exchange_on_a_compressed_plan(lib):
 
 
 def test_exchange_full_size_180_with_90_orbitals(lib):
-    """Eight products meet 1e-7 against the FP64 path; the six-product error is stated (1.6e-7
-    measured: the contraction over 90 orbitals x n^3 cancels more than B's)."""
+    """Six and eight products meet 1e-7 against the FP64 path (six: 8.6e-8 measured with the
+    8/12/12-bit slices and 128-deep drains, 1.6e-7 with 8/11/11-bit slices and 256-deep ones: the
+    contraction over 90 orbitals x n^3 cancels more than B's)."""
     import time
     import torch
     m = synth.workload_spd()
@@ -108,4 +109,4 @@ def test_exchange_full_size_180_with_90_orbitals(lib):
     err8 = rel_fro(res["split_f16_8"][0], res["fp64"][0])
     print(f"exchange, 180 functions, 90 orbitals: split_f16 {res['split_f16'][1] * 1e3:.1f} ms (rel. error "
           f"{err6:.3e}), split_f16_8 {res['split_f16_8'][1] * 1e3:.1f} ms ({err8:.3e}), FP64 {res['fp64'][1] * 1e3:.1f} ms")
-    assert err8 <= 1e-7 and err6 <= 1e-6
+    assert err8 <= 1e-7 and err6 <= 1e-7
