@@ -68,6 +68,68 @@ __global__ void __launch_bounds__(1024) k_split_rows_reg(const double* __restric
     slice_store(0.0, e, false, nslices, r * kpad + i, s0, s1, s2, s1h);
 }
 
+// Short rows (padded length at most 256): one warp per row, eight consecutive elements per lane
+// (16-byte loads where the rows allow them, one 16-byte store per plane); the exponent and the
+// slices are those of the one-block-per-row kernels.
+__global__ void __launch_bounds__(256) k_split_rows_warp(const double* __restrict__ src, int64_t rows, int64_t k,
+                                                         int64_t ld, int64_t kpad, uint16_t* __restrict__ s0,
+                                                         uint16_t* __restrict__ s1, uint16_t* __restrict__ s2,
+                                                         uint16_t* __restrict__ s1h, int* __restrict__ expo,
+                                                         int nslices) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= rows) return;  // the whole warp: r is the same on its lanes
+  const double* x = src + r * ld;
+  const bool vec = (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+  constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFULL;
+  const int64_t i0 = 8 * (int64_t)lane;
+  double v[8];
+  if (vec && i0 + 7 < k) {
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const double2 a = *reinterpret_cast<const double2*>(x + i0 + j);
+      v[j] = a.x;
+      v[j + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = i0 + j < k ? x[i0 + j] : 0.0;
+  }
+  uint64_t mx = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t a = (uint64_t)__double_as_longlong(v[j]) & kMag;
+    mx = a > mx ? a : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t other = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = other > mx ? other : mx;
+  }
+  const double mxd = __longlong_as_double((long long)mx);
+  int e = 0;
+  if (mxd > 0.0) frexp(mxd * (256.0 / 255.0), &e);
+  const bool nz = mxd > 0.0 && e >= -1000;  // rows below ~1e-301 are treated as zero
+  if (lane == 0) expo[r] = e;
+  if (i0 >= kpad) return;
+  SliceBits q[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) q[j] = slice_bits(v[j], e, i0 + j < k && nz, nslices);
+  const int64_t o = r * kpad + i0;
+  *reinterpret_cast<uint4*>(s0 + o) =
+      make_uint4(q[0].s0 | (uint32_t)q[1].s0 << 16, q[2].s0 | (uint32_t)q[3].s0 << 16,
+                 q[4].s0 | (uint32_t)q[5].s0 << 16, q[6].s0 | (uint32_t)q[7].s0 << 16);
+  *reinterpret_cast<uint4*>(s1 + o) =
+      make_uint4(q[0].s1 | (uint32_t)q[1].s1 << 16, q[2].s1 | (uint32_t)q[3].s1 << 16,
+                 q[4].s1 | (uint32_t)q[5].s1 << 16, q[6].s1 | (uint32_t)q[7].s1 << 16);
+  *reinterpret_cast<uint4*>(s2 + o) =
+      make_uint4(q[0].s2 | (uint32_t)q[1].s2 << 16, q[2].s2 | (uint32_t)q[3].s2 << 16,
+                 q[4].s2 | (uint32_t)q[5].s2 << 16, q[6].s2 | (uint32_t)q[7].s2 << 16);
+  if (s1h)
+    *reinterpret_cast<uint4*>(s1h + o) =
+        make_uint4(q[0].s1h | (uint32_t)q[1].s1h << 16, q[2].s1h | (uint32_t)q[3].s1h << 16,
+                   q[4].s1h | (uint32_t)q[5].s1h << 16, q[6].s1h | (uint32_t)q[7].s1h << 16);
+}
+
 // Long rows: two passes over the row (maximum, then slices), four consecutive elements per thread
 // and step: 16-byte loads where the rows allow them (even ld, 16-byte aligned source) and one
 // 8-byte store per plane (kpad is a multiple of 4).
@@ -226,7 +288,14 @@ void launch_split_rows(const double* d_src, int64_t rows, int64_t k, int64_t ld,
     return;
   }
   uint16_t* s1h = (with_s1h || m.eight) ? m.s1h : nullptr;
-  if (rows < 152 && k >= 2048) {
+  if (m.kpad <= 256) {  // short rows (e.g. the N_b-long rows of the exchange's MT): a warp per row
+    tc::k_split_rows_warp<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(d_src, rows, k, ld, m.kpad, m.s0, m.s1, m.s2,
+                                                                      s1h, m.expo, nslices);
+    return;
+  }
+  // few long rows (fewer than four per SM, e.g. the R density rows of a J-build or the N_b rows of
+  // the exchange's last product): eight CTAs per row
+  if ((rows < 4 * 152 && k >= 8192) || (rows < 152 && k >= 2048)) {
     tc::k_split_rows_cluster<<<dim3(tc::kSplitCluster, (unsigned)rows), 256, 0, st>>>(d_src, k, ld, m.kpad, m.s0, m.s1,
                                                                                      m.s2, s1h, m.expo, nslices);
     return;
