@@ -252,6 +252,43 @@ def cpu_oracle_rate(mol, budget_s: float, seed: int = 99):
     return total_entries / total_t, threads, f"{total_entries} random entries (mu,nu,ka,la) of B, Algorithm 1 per entry incl. their pair moments, {total_t:.1f} s"
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model as the kernel reports it (x86: "model name"; Arm: implementer and part)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return platform.machine()
+
+
+def cpu_oracle_thread_scaling(mol, count: int = 2048, seed: int = 98):
+    """The oracle's entries/s on one host core and on all of them, for one fixed sample of `count`
+    entries (the same indices, so the same pair moments to compute)."""
+    import numpy as np
+    import oracle
+    idx = np.random.default_rng(seed).integers(0, mol.nbf, size=(count, 4)).astype(np.int32)
+    out = {"sample": f"{count} random entries, the same for both"}
+    for key, threads in (("one_core", 1), ("all_cores", os.cpu_count() or 1)):
+        o = oracle.Oracle.from_molecule(mol)
+        t0 = time.perf_counter()
+        o.entries(idx, threads=threads)
+        out[key] = count / (time.perf_counter() - t0)
+        del o
+    out["cores"] = os.cpu_count() or 1
+    out["cpu_model"] = host_cpu_model()
+    return out
+
+
 def cpu_oracle_jbuild_rate(mol, R: int = 32, seed: int = 4242):
     """J-builds/s of the FP64 oracle's factored form (eq. coulapprox with the Kronecker mode
     products of eq. ig1) on R densities in one call, all host cores; the moments are computed by
@@ -675,6 +712,7 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(mol, budget_s=15.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu["threads_scaling"] = cpu_oracle_thread_scaling(mol)
         if not args.no_jbuild:
             jr, jsample = cpu_oracle_jbuild_rate(mol)
             cpu["jbuilds_per_s"] = jr
